@@ -1,0 +1,373 @@
+"""Benchmark: 3D Ising HOTRG, chi = 16, steps/s on one GB300 (per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|fp64]
+                    [--impl ours|reference]
+
+Workload: d = 3, chi = 16, beta = 0.2216544, h = 0, axes cycling z, x, y.  The
+first three steps grow the bonds 2 -> 4 -> 16 and are not timed; then W
+steady-state warm-up steps and K timed steps, each one full coarse-graining
+(permutation, FP64 environments, Jacobi, choice/truncation, prime chain,
+bottleneck, non-prime chain, trace/normalisation).  The local tensor (134 MB
+FP64) and the per-slice operands (GBs) exceed the 129 MB L2.
+
+Multi-GPU: independent replicas (one run per rank), weak scaling, no
+collective on the data path; rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D, CHI, BETA, H = 3, 16, 0.2216544, 0.0
+FIRST_AXIS = 2          # z, then x, y
+GROWTH_STEPS = 3
+WORKLOAD = "ising3d_chi16"
+METRIC = "3D-Ising chi=16 HOTRG steps/s, split-BF16 vs FP64, rel err in f<=1e-7; TFLOP/s"
+
+
+def axes_for(n):
+    return [(FIRST_AXIS + s) % D for s in range(n)]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def load_golden():
+    path = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".jsonl")
+    out = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                r = json.loads(line)
+                if r.get("kind") == "step":
+                    out[r["step"]] = r["ln_z_per_site"]
+    except OSError:
+        pass
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--id={self.index}",
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle legs (CPU): bounded samples of one steady-state step
+# ---------------------------------------------------------------------------
+
+def oracle_steady_tensor():
+    from oracle import hotrg_oracle as o
+    run = o.HotrgRun(D, BETA, H)
+    for a in axes_for(GROWTH_STEPS):
+        run.step(a, CHI)
+    return run
+
+
+def oracle_step_sample(run, axis, sample_iters):
+    """Time one oracle step on a sample: environments + eigen-solver in full,
+    `sample_iters` of the (c'_0, n') contraction iterations; return the
+    extrapolated seconds of the whole step."""
+    import itertools
+
+    import numpy as np
+
+    from oracle import hotrg_oracle as o
+    t0 = time.perf_counter()
+    tp = o.to_paper_order(run.t, axis)
+    nxt = o.next_axes(D, axis)
+    legs = [o.choose_isometry(tp, j, CHI, nxt[j - 1]) for j in range(1, D)]
+    t_env = time.perf_counter() - t0
+    us = [leg.u for leg in legs]
+    chi_c = tp.shape[2 * D - 2]
+    nprimes = list(itertools.product(*[range(u.shape[1]) for u in us]))
+    total_iters = chi_c * len(nprimes)
+    t1 = time.perf_counter()
+    that_mat = o.hat_matrix(tp)
+    done = 0
+    for c0p in range(chi_c):
+        for npr in nprimes:
+            o.new_tensor_slab(tp, us, c0p, npr, that_mat)
+            done += 1
+            if done >= sample_iters:
+                break
+        if done >= sample_iters:
+            break
+    t_con = time.perf_counter() - t1
+    return t_env + t_con * total_iters / done, dict(env_eig_s=round(t_env, 3),
+                                                   contraction_iters_timed=done,
+                                                   contraction_iters_total=total_iters)
+
+
+def cpu_baseline_leg():
+    run = oracle_steady_tensor()
+    est, info = oracle_step_sample(run, axes_for(GROWTH_STEPS + 1)[-1], 48)
+    return {"value": 1.0 / est, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one steady-state 3D chi=16 step: environments + Jacobi in full "
+                       f"({info['env_eig_s']} s), {info['contraction_iters_timed']} of "
+                       f"{info['contraction_iters_total']} (c'_0, n') contraction iterations, "
+                       f"extrapolated to the whole step"),
+            "extrapolated_s_per_step": est}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    run = oracle_steady_tensor()
+    axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)[GROWTH_STEPS:]
+    ests = []
+    for i, a in enumerate(axes):
+        est, info = oracle_step_sample(run, a, 16)
+        if i >= args.warmup:
+            ests.append(est)
+    mean = sum(ests) / len(ests)
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / mean, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D Ising HOTRG d=3 chi=16 beta=0.2216544 h=0, axes z,x,y",
+                       "sample": "each step: oracle environments + Jacobi in full and 16 of 4096 "
+                                 "contraction iterations, extrapolated"},
+            "cpu_baseline": {"value": 1.0 / mean, "unit": "steps/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "16 of 4096 contraction iterations per step"},
+            "e2e": {"value": 1.0 / mean, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    import paper_2110_03607_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    stream = torch.cuda.current_stream()
+
+    g = pkg.Hotrg(D, BETA, H, precision=prec)
+    axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
+    lnz_by_step = {}
+    for i, a in enumerate(axes[: GROWTH_STEPS + args.warmup]):
+        g.step(a, CHI)
+        lnz_by_step[i + 1] = g.free_energy()[0]
+    pkg.hotrg_profile(g.ctx, True)
+    timed_axes = axes[GROWTH_STEPS + args.warmup:]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    phase_sum, launch_sum = {}, {}
+    launches0 = pkg.hotrg_launch_count(g.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    step_no = GROWTH_STEPS + args.warmup
+    for a in timed_axes:
+        g.step(a, CHI)
+        step_no += 1
+        # per-phase event times of this step (reading them synchronises the stream
+        # once per step; the step itself is ~10^2 ms of device work)
+        ms, nl, f64 = pkg.hotrg_step_times(g.ctx)
+        for k, v in ms.items():
+            phase_sum[k] = phase_sum.get(k, 0.0) + v
+            launch_sum[k] = launch_sum.get(k, 0) + nl[k]
+        lnz_by_step[step_no] = g.free_energy()[0]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = pkg.hotrg_launch_count(g.ctx) - launches0
+    sampler.stop()
+    clocks = sampler.summary()
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    K = len(timed_axes)
+    value = world * K / (elapsed_ms / 1000.0)
+
+    # ---- accuracy against the FP64 oracle's per-step ln Z / V (tests/golden)
+    golden = load_golden()
+    errs = {s: abs(lnz_by_step[s] - golden[s]) / abs(golden[s]) for s in lnz_by_step if s in golden}
+    rel_err = max(errs.values()) if errs else None
+
+    # ---- roofline of the bottleneck GEMM (algorithmic flops per c'-slice launch)
+    R = CHI ** D                   # rows = cols of T at steady state
+    Ns = CHI ** (2 * (D - 1))      # (n', n~) columns per c'-slice
+    flops_per_launch = 2.0 * R * R * Ns
+    peaks, peak_src = load_peaks()
+    bn_launches = launch_sum.get("bottleneck", 0)
+    bn_ms = phase_sum.get("bottleneck", 0.0) / max(1, bn_launches)
+    nterms = {"bf16x6": 6, "bf16x3": 3, "fp64": 1}[args.precision]
+    achieved = flops_per_launch / (bn_ms / 1000.0) / 1e12 if bn_ms > 0 else None
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25 if achieved else None, "traffic": None,
+                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+    else:
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                "issued_tflops": achieved * nterms if achieved else None,
+                "issued_frac": achieved * nterms / peak if achieved else None,
+                "algorithmic_flops_per_launch": flops_per_launch,
+                "avg_launch_ms": bn_ms}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        t_host = pkg.hotrg_tensor(g.ctx)
+        pinned = torch.empty(t_host.size, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[:] = t_host.reshape(-1)
+        out = torch.empty_like(pinned).pin_memory()
+        pkg.hotrg_profile(g.ctx, False)
+        e2e_axes = axes_for(GROWTH_STEPS + args.warmup + K + 4)[-4:]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        chis = pkg.hotrg_bond_dims(g.ctx)[:D]
+        for a in e2e_axes:
+            pkg.hotrg_set_tensor(g.ctx, chis, pinned)      # host -> device
+            h2d += pinned.numel() * 8
+            g.step(a, CHI)
+            pkg.hotrg_free_energy(g.ctx)                    # 16-byte read-back
+            pkg.hotrg_tensor(g.ctx, out.numpy().reshape([c for c in chis for _ in (0, 1)]))
+            d2h += out.numel() * 8 + 16
+            pinned, out = out, pinned
+        dt = time.perf_counter() - t0
+        e2e = {"value": len(e2e_axes) / dt, "unit": "steps/s",
+               "h2d_bytes_per_step": h2d // len(e2e_axes), "d2h_bytes_per_step": d2h // len(e2e_axes),
+               "steps": len(e2e_axes)}
+    g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg()
+
+    if rank == 0:
+        mean_phase = {k: round(v / K, 3) for k, v in phase_sum.items()}
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
+                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ",
+                      "fp64": "f64"}[args.precision],
+            "data": "synthetic (Ising initial tensor from beta, h; no dataset)",
+            "config": {"workload": "3D Ising HOTRG d=3 chi=16 beta=0.2216544 h=0, axes z,x,y; "
+                                   f"steps 1-3 (bond growth) untimed, {args.warmup} warm-up steps, "
+                                   f"steps {GROWTH_STEPS + args.warmup + 1}-{GROWTH_STEPS + args.warmup + K} timed",
+                       "precision": args.precision, "l2": "inputs larger than L2 (T 134 MB, "
+                                                          "per-slice operands GBs)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "rel_err_lnz_per_site_vs_oracle": rel_err,
+            "rel_err_steps_compared": len(errs),
+            "phases_ms_per_step": mean_phase,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * hotrg.h -- C ABI of the GB300 HOTRG coarse-graining library (libhotrg.so).
+ *
+ * Method: Yamashita & Sakurai, "A Parallel Computing Method for the Higher
+ * Order Tensor Renormalization Group" (arXiv:2110.03607).  One call of
+ * hotrg_step() is one coarse-graining along one lattice axis (Sec. 2, Eq.
+ * CoarseGrainingProcedure_d; Sec. 4.2): environment matrices A^(j), A'^(j)
+ * (Sec. 3.2), their eigen-decomposition (Sec. 4.2.5), the choice and
+ * truncation of the isometries (Secs. 4.2.6-4.2.8), the contraction for the
+ * new tensor (Sec. 4.2.9), and the trace / normalisation / ln Z bookkeeping
+ * (Secs. 4.1.1, 4.2.11-4.2.16).  Everything after the argument checks runs
+ * as CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every function returns a status (HOTRG_OK or a negative HOTRG_E*);
+ *    outputs go through out-pointers.  hotrg_strerror() names a status.
+ *  - The library owns all device memory of a context.  It allocates with
+ *    cudaMalloc, or through the hook given to hotrg_set_allocator().
+ *  - hotrg_step() only enqueues work on the context's stream and returns.
+ *    The read-back calls (hotrg_free_energy, hotrg_observables,
+ *    hotrg_isometry, hotrg_spectrum, hotrg_tensor) synchronise that stream.
+ *  - Device-side failures (a non-positive or non-finite trace, a Jacobi
+ *    sweep cap, a bounded wait that expired) are recorded in a device status
+ *    word and returned by the next read-back call.  After any failure other
+ *    than HOTRG_EINVAL the context is poisoned: further calls return
+ *    HOTRG_ESTATE until it is freed.
+ *  - Tensor interchange layout: a local tensor of a d-dimensional lattice is
+ *    a dense, row-major array with 2d axes (x_1, x_1', x_2, x_2', ...,
+ *    x_d, x_d'), the index order of Eq. (2.4); axis k (0-based) has bond
+ *    dimension dims[2k] = dims[2k+1].  Pointers passed for tensors may be
+ *    host or device pointers (they are copied with cudaMemcpyDefault).
+ *  - Lattice axes are 0-based: 0 = x, 1 = y, 2 = z, 3 = w.
+ */
+#ifndef HOTRG_H
+#define HOTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hotrg_ctx hotrg_ctx;
+
+enum hotrg_status {
+  HOTRG_OK = 0,
+  HOTRG_EINVAL = -1,    /* bad argument or buffer too small (size out-params still set) */
+  HOTRG_ENOMEM = -2,    /* device allocation failed */
+  HOTRG_ECUDA = -3,     /* a CUDA runtime or driver call failed */
+  HOTRG_ENUMERIC = -4,  /* trace of a new tensor <= 0 or not finite */
+  HOTRG_ENOTCONV = -5,  /* Jacobi eigen-solver hit its sweep cap */
+  HOTRG_ETIMEOUT = -6,  /* a bounded device-side wait expired */
+  HOTRG_ESTATE = -7     /* context poisoned by an earlier failure, or no step yet */
+};
+
+/* Arithmetic of the contractions (prime chain, bottleneck, non-prime chain).
+ * The environment matrices, the eigen-solver and the ln Z accumulation are
+ * FP64 in every mode.  BF16X3: operands split into 2 BF16 pieces, 3 piece
+ * products, FP32 accumulation.  BF16X6: 3 pieces, 6 products.  FP64: plain
+ * FP64 everywhere. */
+enum hotrg_precision {
+  HOTRG_PREC_FP64 = 0,
+  HOTRG_PREC_BF16X3 = 1,
+  HOTRG_PREC_BF16X6 = 2
+};
+
+/* Start a run from the Ising initial tensor of Sec. 2, Eq. (2.4):
+ * W_{s s'} = exp(beta s s'), X = U sqrt(Lambda), V_s = exp(beta h s),
+ * sigma_0 = +1, sigma_1 = -1; bond dimension 2 on every leg.  The tensor is
+ * normalised by f^(0) = 1/Tr T (Sec. 4.2.1) and ln Z^(0) = ln Tr T^(0).
+ * d in [2, 4]; beta >= 0 (beta = 0 allowed; sqrt(sinh beta) is imaginary
+ * for beta < 0).  On success *out owns a new context (default stream 0,
+ * precision BF16X6).  Errors: EINVAL, ENOMEM, ECUDA. */
+int hotrg_init_ising(int d, double beta, double h, hotrg_ctx** out);
+
+/* Start a run from a caller-given initial tensor T (interchange layout,
+ * dims[2k] = dims[2k+1] = chis[k], 1 <= chis[k] <= 32).  Normalised as in
+ * hotrg_init_ising.  beta is used only to report f = -(ln Z/V)/beta. */
+int hotrg_init_tensor(int d, const int* chis, const double* T, double beta, hotrg_ctx** out);
+
+/* Replace the current (normalised) local tensor of a run by T with bond
+ * dimensions chis, keeping the run's K / ln Z bookkeeping (a resume from a
+ * checkpoint).  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
+int hotrg_set_tensor(hotrg_ctx* ctx, const int* chis, const double* T);
+
+/* Use `stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work of the context.  NULL = the legacy default stream. */
+int hotrg_set_stream(hotrg_ctx* ctx, void* stream);
+
+/* Route the context's device allocations through alloc/free (e.g. a caching
+ * allocator).  alloc(bytes, user) returns a device pointer or NULL;
+ * free(ptr, user) releases it.  Buffers already held are released through
+ * the previous allocator first.  Pass NULL, NULL to return to cudaMalloc. */
+typedef void* (*hotrg_alloc_fn)(size_t bytes, void* user);
+typedef void (*hotrg_free_fn)(void* ptr, void* user);
+int hotrg_set_allocator(hotrg_ctx* ctx, hotrg_alloc_fn alloc, hotrg_free_fn free_fn, void* user);
+
+/* Select the contraction arithmetic (enum hotrg_precision). */
+int hotrg_set_precision(hotrg_ctx* ctx, int mode);
+
+/* In the BF16 modes, run the contraction of a step in FP64 when its
+ * bottleneck needs fewer than `flops` floating-point operations (the early
+ * steps of a run, while the bonds grow: they are cheap, and an error made
+ * in step p weighs 2^-p in ln Z / V).  Default 2^36; 0 = never. */
+int hotrg_set_fp64_threshold(hotrg_ctx* ctx, double flops);
+
+/* Record CUDA events around the phases of every later step (enable = 1) or
+ * stop (0).  hotrg_step_times() then returns, after synchronising, the
+ * milliseconds of the last step per phase: [0] leg permutation, [1]
+ * environment Grams and A assembly, [2] Jacobi, [3] choice/truncation,
+ * [4] BF16 split of T, [5] prime-side chain, [6] bottleneck GEMM, [7]
+ * non-prime chain, [8] trace / normalisation; *n = 9.  launches[k] = number
+ * of kernels timed in phase k (the bottleneck: one per c'-slice).
+ * *contraction_fp64 = 1 if the last step's contraction ran in FP64. */
+int hotrg_profile(hotrg_ctx* ctx, int enable);
+int hotrg_step_times(hotrg_ctx* ctx, double ms[16], int launches[16], int* n, int* contraction_fp64);
+
+/* One coarse-graining along lattice axis `axis` in [0, d) with bond-
+ * dimension parameter chi >= 1 (Sec. 2: chi_j^new = min(chi_j^2, chi) on
+ * every transverse leg j; the axis's own bond is unchanged).  Transverse
+ * legs are labelled Next j = axis (axis + j) mod d (Sec. 3.1.2).  The new
+ * tensor is normalised by 1/Tr (Secs. 4.2.14-4.2.16).  Asynchronous.
+ * Errors: EINVAL (axis out of range, chi outside [1, 32]),
+ * ENOMEM, ECUDA, ESTATE. */
+int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
+
+/* The isometry U~ chosen by the last step for lattice axis `leg` (a
+ * transverse axis of that step): a rows x cols row-major FP64 matrix, rows
+ * = chi_leg^2 indexed by (hat + check * chi_leg) (Sec. 3.2), cols =
+ * chi_leg^new; *chosen_prime = 1 if U'^(j) (prime side) was chosen, else 0
+ * (Sec. 4.2.7).  Each column is sign-fixed: its pivot entry (the lowest row
+ * whose magnitude is within 1e-6 of the column's largest) is positive.
+ * cap is the capacity of U in elements.  Errors: EINVAL (leg not transverse
+ * in the last step, cap too small), ESTATE, a recorded device failure. */
+int hotrg_isometry(hotrg_ctx* ctx, int leg, double* U, int64_t cap, int* rows,
+                   int* cols, int* chosen_prime);
+
+/* Eigenvalues, descending, of A^(j) (prime = 0) or A'^(j) (prime = 1) for
+ * lattice axis `leg` in the last step (Sec. 4.2.5); *n = chi_leg^2. */
+int hotrg_spectrum(hotrg_ctx* ctx, int leg, int prime, double* lam, int64_t cap, int* n);
+
+/* Discarded sums epsilon^(j), epsilon'^(j) of the last step (Sec. 2). */
+int hotrg_truncation(hotrg_ctx* ctx, int leg, double* eps, double* eps_prime);
+
+/* ln Z^(p) / V^(p) with V^(p) = 2^p (Sec. 4.1.1, Eqs. eq_lnZ, K_recurrence)
+ * after p steps, and f = -(ln Z/V) / beta (NaN when beta = 0). */
+int hotrg_free_energy(hotrg_ctx* ctx, double* lnZ_per_site, double* f_per_site);
+
+/* Tr T^(p) of the last new tensor before normalisation (= trace Y), the
+ * Gu-Wen ratio X = (trace Y)^2 / trace(Y^2) (Sec. 4.1.2), and p. */
+int hotrg_observables(hotrg_ctx* ctx, double* trace, double* gu_wen_X, int* nsteps);
+
+/* Current bond dimension of each lattice axis (dims[k], k < d). */
+int hotrg_bond_dims(hotrg_ctx* ctx, int dims[4]);
+
+/* Copy the current normalised local tensor in interchange layout.  dims
+ * receives the 2d extents.  Errors: EINVAL if cap is too small. */
+int hotrg_tensor(hotrg_ctx* ctx, double* T, int64_t cap, int dims[8]);
+
+/* The bottleneck contraction of Eq. (BottleneckPart) on its own:
+ * C[M][N] = sum_k A[M][K] B[N][K] (both operands K-contiguous, row-major,
+ * FP64 in and out) computed with the kernels of precision `mode` (split-BF16
+ * pieces on the tensor cores with FP32 accumulation, or FP64 DFMA tiles).
+ * A, B, C may be host or device pointers.  Synchronous; allocates and frees
+ * its own device scratch.  1 <= M, N, K <= 2^20 and M*K, N*K, M*N <= 2^31.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* B, double* C);
+
+/* Bytes of device memory the context holds now. */
+int hotrg_device_bytes(hotrg_ctx* ctx, size_t* bytes);
+
+/* Number of kernels the context has launched since it was created. */
+int hotrg_launch_count(hotrg_ctx* ctx, int64_t* launches);
+
+void hotrg_free(hotrg_ctx* ctx);
+const char* hotrg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOTRG_H */

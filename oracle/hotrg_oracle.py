@@ -345,7 +345,17 @@ def _contract_axis(x: np.ndarray, axis: int, m: np.ndarray) -> np.ndarray:
     return np.moveaxis(y, -1, axis)
 
 
-def new_tensor_slab(tp: np.ndarray, us: list[np.ndarray], c0p: int, nprime: tuple) -> np.ndarray:
+def hat_matrix(tp: np.ndarray) -> np.ndarray:
+    """The c-fixed tensors of every c0 as one matrix [(c0, n^..), (n^'.., rho)]
+    (Sec. 3.2); loop-invariant in the contraction of Sec. 4.2.9."""
+    d = tp.ndim // 2
+    that = np.moveaxis(tp, 2 * d - 2, 0)       # [c0, n^.., n^'.., rho]
+    rows = int(np.prod(that.shape[:d]))
+    return np.ascontiguousarray(that).reshape(rows, -1)
+
+
+def new_tensor_slab(tp: np.ndarray, us: list[np.ndarray], c0p: int, nprime: tuple,
+                    that_mat: np.ndarray | None = None) -> np.ndarray:
     """Elements T^new_{n_{d-1}..n_1 n'_{d-1}..n'_1 c c'} for c' = c0p and one fixed
     n' = (n'_1, .., n'_{d-1}), for every c and n (Sec. 4.2.9).
 
@@ -367,11 +377,14 @@ def new_tensor_slab(tp: np.ndarray, us: list[np.ndarray], c0p: int, nprime: tupl
         cchk = _contract_axis(cchk, _pos_np(d, j), u_col)
     # cchk axes: n~_{d-1}..n~_1, n^'_{d-1}..n^'_1, rho
     # second step (bottleneck): C^_{n~.. n^..} = sum_{n^', rho} T^_{n^.. n^'.. rho} C~_{n~.. n^'.. rho}
-    # T-hat^{c=c0}_{n^.. n^'.. rho} = T_{n^.. n^'.. c0 rho}, all c0 at once
-    that = np.moveaxis(tp, 2 * d - 2, 0)       # [c0, n^.., n^'.., rho]
-    contr_hat = list(range(d, 2 * d))          # n^'.., rho of that
-    contr_chk = list(range(d - 1, 2 * d - 1))  # n^'.., rho of cchk
-    chat = np.tensordot(that, cchk, axes=(contr_hat, contr_chk))
+    # T-hat^{c=c0}_{n^.. n^'.. rho} = T_{n^.. n^'.. c0 rho}, all c0 at once, as the
+    # matrix [(c0, n^..), (n^'.., rho)]; C~ as [(n~..), (n^'.., rho)]
+    if that_mat is None:
+        that_mat = hat_matrix(tp)
+    chi_c = tp.shape[2 * d - 2]
+    nchk = cchk.shape[: d - 1]
+    chat = that_mat @ cchk.reshape(int(np.prod(nchk)), -1).T
+    chat = chat.reshape((chi_c,) + tp.shape[: d - 1] + nchk)
     # chat axes: c0, n^_{d-1}..n^_1, n~_{d-1}..n~_1 -> paper order c0, n~.., n^..
     to_paper = [0] + list(range(d, 2 * d - 1)) + list(range(1, d))
     chat = np.transpose(chat, to_paper)
@@ -396,9 +409,10 @@ def new_tensor(tp: np.ndarray, us: list[np.ndarray], progress=None) -> np.ndarra
     chi_new = [u.shape[1] for u in us]          # j = 1..d-1
     shape = [chi_new[j - 1] for j in range(d - 1, 0, -1)] * 2 + [chi_c, chi_c]
     out = np.zeros(shape)
+    that_mat = hat_matrix(tp)
     for c0p in range(chi_c):
         for nprime in itertools.product(*[range(k) for k in chi_new]):
-            slab = new_tensor_slab(tp, us, c0p, nprime)   # [c0, n_{d-1}..n_1]
+            slab = new_tensor_slab(tp, us, c0p, nprime, that_mat)   # [c0, n_{d-1}..n_1]
             idx = tuple(nprime[j - 1] for j in range(d - 1, 0, -1))
             # out[n_{d-1}..n_1, n'_{d-1}..n'_1, c, c'] = slab[c, n..]
             out[(Ellipsis,) + idx + (slice(None), c0p)] = np.moveaxis(slab, 0, -1)

@@ -1,0 +1,287 @@
+"""ctypes binding of libhotrg.so: argument marshalling only.
+
+Every function below has the name of the C entry point it wraps and raises
+HotrgError on a non-zero status.  Tensors cross the boundary as numpy
+float64 arrays in the interchange layout (axes x_1, x_1', ..., x_d, x_d'),
+or as any object exposing a device/host pointer via ``data_ptr()`` (torch).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+PREC_FP64 = 0
+PREC_BF16X3 = 1
+PREC_BF16X6 = 2
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class HotrgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = load().hotrg_strerror(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def library_path() -> str:
+    return os.environ.get("HOTRG_LIBRARY", os.path.join(_PKG, "libhotrg.so"))
+
+
+def load():
+    """Load libhotrg.so (raises if it was not built: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libhotrg.so not found at {path}; build it with "
+                          "`python -m paper_2110_03607_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    I64 = ctypes.c_int64
+    sig = {
+        "hotrg_init_ising": (I, [I, D, D, ctypes.POINTER(P)]),
+        "hotrg_init_tensor": (I, [I, ctypes.POINTER(I), P, D, ctypes.POINTER(P)]),
+        "hotrg_set_tensor": (I, [P, ctypes.POINTER(I), P]),
+        "hotrg_set_stream": (I, [P, P]),
+        "hotrg_set_allocator": (I, [P, _ALLOC_FN, _FREE_FN, P]),
+        "hotrg_set_precision": (I, [P, I]),
+        "hotrg_step": (I, [P, I, I]),
+        "hotrg_isometry": (I, [P, I, P, I64, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "hotrg_spectrum": (I, [P, I, I, P, I64, ctypes.POINTER(I)]),
+        "hotrg_truncation": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hotrg_free_energy": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hotrg_observables": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "hotrg_bond_dims": (I, [P, ctypes.POINTER(I)]),
+        "hotrg_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
+        "hotrg_gemm_nt": (I, [I, I, I, I, P, P, P]),
+        "hotrg_set_fp64_threshold": (I, [P, D]),
+        "hotrg_profile": (I, [P, I]),
+        "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "hotrg_launch_count": (I, [P, ctypes.POINTER(I64)]),
+        "hotrg_free": (None, [P]),
+        "hotrg_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise HotrgError(status, where)
+
+
+def _ptr(buf):
+    if hasattr(buf, "data_ptr"):
+        return ctypes.c_void_p(buf.data_ptr())
+    return buf.ctypes.data_as(ctypes.c_void_p)
+
+
+def hotrg_init_ising(d: int, beta: float, h: float):
+    ctx = ctypes.c_void_p()
+    _check(load().hotrg_init_ising(d, beta, h, ctypes.byref(ctx)), "hotrg_init_ising")
+    return ctx
+
+
+def hotrg_init_tensor(d: int, chis, t, beta: float):
+    arr = np.ascontiguousarray(t, dtype=np.float64) if not hasattr(t, "data_ptr") else t
+    c = (ctypes.c_int * 4)(*list(chis) + [0] * (4 - len(chis)))
+    ctx = ctypes.c_void_p()
+    _check(load().hotrg_init_tensor(d, c, _ptr(arr), beta, ctypes.byref(ctx)), "hotrg_init_tensor")
+    return ctx
+
+
+def hotrg_set_tensor(ctx, chis, t):
+    arr = np.ascontiguousarray(t, dtype=np.float64) if not hasattr(t, "data_ptr") else t
+    c = (ctypes.c_int * 4)(*list(chis) + [0] * (4 - len(chis)))
+    _check(load().hotrg_set_tensor(ctx, c, _ptr(arr)), "hotrg_set_tensor")
+
+
+def hotrg_set_stream(ctx, stream_handle: int):
+    _check(load().hotrg_set_stream(ctx, ctypes.c_void_p(stream_handle)), "hotrg_set_stream")
+
+
+def hotrg_set_precision(ctx, mode: int):
+    _check(load().hotrg_set_precision(ctx, mode), "hotrg_set_precision")
+
+
+def hotrg_step(ctx, axis: int, chi: int):
+    _check(load().hotrg_step(ctx, axis, chi), "hotrg_step")
+
+
+def hotrg_isometry(ctx, leg: int):
+    rows, cols, prime = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib = load()
+    st = lib.hotrg_isometry(ctx, leg, None, 0, ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(prime))
+    if st not in (0, -1) or rows.value == 0:
+        _check(st, "hotrg_isometry")
+    u = np.empty((rows.value, cols.value), dtype=np.float64)
+    _check(lib.hotrg_isometry(ctx, leg, _ptr(u), u.size, ctypes.byref(rows), ctypes.byref(cols),
+                              ctypes.byref(prime)), "hotrg_isometry")
+    return u, bool(prime.value)
+
+
+def hotrg_spectrum(ctx, leg: int, prime: int):
+    n = ctypes.c_int()
+    lib = load()
+    st = lib.hotrg_spectrum(ctx, leg, prime, None, 0, ctypes.byref(n))
+    if st not in (0, -1) or n.value == 0:
+        _check(st, "hotrg_spectrum")
+    lam = np.empty(n.value, dtype=np.float64)
+    _check(lib.hotrg_spectrum(ctx, leg, prime, _ptr(lam), lam.size, ctypes.byref(n)), "hotrg_spectrum")
+    return lam
+
+
+def hotrg_truncation(ctx, leg: int):
+    e, ep = ctypes.c_double(), ctypes.c_double()
+    _check(load().hotrg_truncation(ctx, leg, ctypes.byref(e), ctypes.byref(ep)), "hotrg_truncation")
+    return e.value, ep.value
+
+
+def hotrg_free_energy(ctx):
+    lnz, f = ctypes.c_double(), ctypes.c_double()
+    _check(load().hotrg_free_energy(ctx, ctypes.byref(lnz), ctypes.byref(f)), "hotrg_free_energy")
+    return lnz.value, f.value
+
+
+def hotrg_observables(ctx):
+    tr, x, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().hotrg_observables(ctx, ctypes.byref(tr), ctypes.byref(x), ctypes.byref(n)),
+           "hotrg_observables")
+    return tr.value, x.value, n.value
+
+
+def hotrg_bond_dims(ctx):
+    dims = (ctypes.c_int * 4)()
+    _check(load().hotrg_bond_dims(ctx, dims), "hotrg_bond_dims")
+    return list(dims)
+
+
+def hotrg_tensor(ctx, out=None):
+    dims = (ctypes.c_int * 8)()
+    lib = load()
+    lib.hotrg_tensor(ctx, None, 0, dims)
+    shape = [x for x in dims if x > 0]
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    n = int(np.prod(shape))
+    _check(lib.hotrg_tensor(ctx, _ptr(out), n, dims), "hotrg_tensor")
+    return out
+
+
+def hotrg_gemm_nt(mode: int, a, b):
+    """C = A . B^T with the bottleneck kernel of `mode` (numpy float64 in and out)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m, k = a.shape
+    n, k2 = b.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    c = np.empty((m, n), dtype=np.float64)
+    _check(load().hotrg_gemm_nt(mode, m, n, k, _ptr(a), _ptr(b), _ptr(c)), "hotrg_gemm_nt")
+    return c
+
+
+def hotrg_set_fp64_threshold(ctx, flops: float):
+    _check(load().hotrg_set_fp64_threshold(ctx, float(flops)), "hotrg_set_fp64_threshold")
+
+
+def hotrg_profile(ctx, enable: bool):
+    _check(load().hotrg_profile(ctx, 1 if enable else 0), "hotrg_profile")
+
+
+PHASES = ["permute", "environment", "jacobi", "select", "split", "prime_chain", "bottleneck",
+          "nonprime_chain", "trace_norm"]
+
+
+def hotrg_step_times(ctx):
+    ms = (ctypes.c_double * 16)()
+    nl = (ctypes.c_int * 16)()
+    n, f64 = ctypes.c_int(), ctypes.c_int()
+    _check(load().hotrg_step_times(ctx, ms, nl, ctypes.byref(n), ctypes.byref(f64)), "hotrg_step_times")
+    return ({PHASES[k]: ms[k] for k in range(n.value)}, {PHASES[k]: nl[k] for k in range(n.value)},
+            bool(f64.value))
+
+
+def hotrg_device_bytes(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(load().hotrg_device_bytes(ctx, ctypes.byref(b)), "hotrg_device_bytes")
+    return b.value
+
+
+def hotrg_launch_count(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(load().hotrg_launch_count(ctx, ctypes.byref(n)), "hotrg_launch_count")
+    return n.value
+
+
+def hotrg_free(ctx):
+    load().hotrg_free(ctx)
+
+
+def hotrg_strerror(status: int) -> str:
+    return load().hotrg_strerror(status).decode()
+
+
+class Hotrg:
+    """Owning handle around one context, with torch streams and memory."""
+
+    def __init__(self, d: int, beta: float, h: float = 0.0, precision: int = PREC_BF16X6,
+                 use_torch: bool = True, tensor=None, chis=None, fp64_below: float | None = None):
+        self.d = d
+        self.beta = beta
+        if tensor is None:
+            self.ctx = hotrg_init_ising(d, beta, h)
+        else:
+            self.ctx = hotrg_init_tensor(d, chis, tensor, beta)
+        self._cb = None
+        if use_torch:
+            self.use_torch()
+        hotrg_set_precision(self.ctx, precision)
+        if fp64_below is not None:
+            hotrg_set_fp64_threshold(self.ctx, fp64_below)
+
+    def use_torch(self):
+        import torch
+
+        def _alloc(nbytes, _user):
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+
+        def _free(ptr, _user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        _check(load().hotrg_set_allocator(self.ctx, self._cb[0], self._cb[1], None), "hotrg_set_allocator")
+        hotrg_set_stream(self.ctx, torch.cuda.current_stream().cuda_stream)
+
+    def step(self, axis: int, chi: int):
+        hotrg_step(self.ctx, axis, chi)
+
+    def free_energy(self):
+        return hotrg_free_energy(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            hotrg_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

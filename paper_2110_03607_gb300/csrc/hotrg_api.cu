@@ -1,0 +1,1077 @@
+// C ABI of libhotrg: context, device memory, and the orchestration of one
+// HOTRG coarse-graining step on one stream (Sec. 4.2 of Yamashita & Sakurai,
+// arXiv:2110.03607).
+//
+// Device layout of the local tensor ("slot layout"): a row-major matrix
+// T[(i_0, .., i_{d-1})][(i_0', .., i_{d-1}')] whose slot s holds lattice axis
+// order[s].  A step along `axis` first permutes T so that slot 0 is the
+// Current direction (c, c') and slot j is Next j (n_j, n_j') -- the index
+// naming of Secs. 3.1.2-3.1.3.  In that layout T is at the same time the
+// c-fixed tensors (rows c) and the c'-fixed tensors (column blocks c') of
+// Sec. 3.2, so the bottleneck of Eq. (BottleneckPart) is one GEMM with T as
+// its left operand, sliced over c'.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "hotrg_internal.cuh"
+#include "../../include/hotrg.h"
+
+using namespace hotrg;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// index names for the chain descriptors
+enum : int {
+  I_C = 1,
+  I_RHO = 2,
+  I_NH = 10,   // n^_j   (hat copy, unprimed)
+  I_NC = 20,   // n~_j   (check copy, unprimed)
+  I_NHP = 30,  // n^'_j  (hat copy, primed)
+  I_NCP = 40,  // n~'_j  (check copy, primed)
+  I_N = 50,    // n_j    (new, unprimed)
+  I_NP = 60    // n'_j   (new, primed)
+};
+
+struct Ix {
+  int name;
+  long long size;
+  long long stride;
+};
+typedef std::vector<Ix> View;
+
+View contiguous(const std::vector<std::pair<int, long long>>& names) {
+  View v(names.size());
+  long long st = 1;
+  for (int k = (int)names.size() - 1; k >= 0; --k) {
+    v[k] = {names[k].first, names[k].second, st};
+    st *= names[k].second;
+  }
+  return v;
+}
+
+long long stride_of(const View& v, int name, bool* found = nullptr) {
+  for (auto& x : v)
+    if (x.name == name) {
+      if (found) *found = true;
+      return x.stride;
+    }
+  if (found) *found = false;
+  return 0;
+}
+
+ChainDesc make_stage(const View& in, const View& out, int a_name, int b_name, int n_name, int chi,
+                     int nn) {
+  ChainDesc d;
+  memset(&d, 0, sizeof(d));
+  View fr;
+  for (auto& o : out)
+    if (o.name != n_name) fr.push_back(o);
+  std::stable_sort(fr.begin(), fr.end(), [](const Ix& a, const Ix& b) { return a.stride < b.stride; });
+  d.ndim = (int)fr.size();
+  d.a_dim = -1;
+  d.total = 1;
+  for (int k = 0; k < d.ndim; ++k) {
+    d.size[k] = fr[k].size;
+    d.out_stride[k] = fr[k].stride;
+    d.in_stride[k] = stride_of(in, fr[k].name);
+    if (fr[k].name == a_name) d.a_dim = k;
+    d.total *= fr[k].size;
+  }
+  d.ka_stride = d.a_dim >= 0 ? 0 : stride_of(in, a_name);
+  d.kb_stride = stride_of(in, b_name);
+  d.n_out_stride = stride_of(out, n_name);
+  d.chi = chi;
+  d.nn = nn;
+  d.npieces = 1;
+  return d;
+}
+
+}  // namespace
+
+struct hotrg_ctx {
+  int d = 0;
+  double beta = 0.0;
+  int chis[kMaxD] = {0, 0, 0, 0};
+  int order[kMaxD] = {0, 1, 2, 3};
+  int p = 0;
+  int precision = HOTRG_PREC_BF16X6;
+  cudaStream_t stream = nullptr;
+  hotrg_alloc_fn afn = nullptr;
+  hotrg_free_fn ffn = nullptr;
+  void* user = nullptr;
+  int poisoned = 0;
+  size_t held = 0;
+  double fp64_below = 68719476736.0;  // 2^36 flops
+  // diagnostic: FP64-accumulating chains around the split-BF16 bottleneck
+  int f64_chains = getenv("HOTRG_DEBUG_F64_CHAINS") ? atoi(getenv("HOTRG_DEBUG_F64_CHAINS")) : 0;
+  // phase timing
+  int profile = 0;
+  int last_fp64 = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next = 0;
+  // last step
+  int last_valid = 0;
+  int last_nlegs = 0;
+  int last_leg_axis[kMaxD - 1] = {0, 0, 0};
+  int last_leg_n[kMaxD - 1] = {0, 0, 0};
+  int last_leg_nnew[kMaxD - 1] = {0, 0, 0};
+  long long last_lam_off[kMaxD - 1] = {0, 0, 0};
+  long long last_u_off[kMaxD - 1] = {0, 0, 0};
+  // buffers
+  Buf T, T2, Xp, parts, S, Amat, W, V, lam, U64, U32, legres, Y, state, counters, sweeps;
+  Buf Ap, Bp, Cb, chA, chB;
+};
+
+namespace {
+
+int dev_alloc(hotrg_ctx* c, Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return HOTRG_OK;
+  if (b.p) {
+    if (c->ffn) c->ffn(b.p, c->user);
+    else cudaFree(b.p);
+    c->held -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = std::max<size_t>(bytes, 256);
+  void* p = nullptr;
+  if (c->afn) {
+    p = c->afn(want, c->user);
+    if (!p) return HOTRG_ENOMEM;
+  } else {
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return HOTRG_ENOMEM;
+    }
+  }
+  b.p = p;
+  b.bytes = want;
+  c->held += want;
+  return HOTRG_OK;
+}
+
+void dev_release(hotrg_ctx* c, Buf& b) {
+  if (!b.p) return;
+  if (c->ffn) c->ffn(b.p, c->user);
+  else cudaFree(b.p);
+  c->held -= b.bytes;
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+cudaEvent_t next_event(hotrg_ctx* c) {
+  if (c->event_next == c->event_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->event_pool.push_back(e);
+  }
+  return c->event_pool[c->event_next++];
+}
+
+// RAII phase mark: records a start/stop event pair on the stream when profiling
+struct Phase {
+  hotrg_ctx* c;
+  int id;
+  cudaEvent_t e0 = nullptr;
+  Phase(hotrg_ctx* c_, int id_) : c(c_), id(id_) {
+    if (c->profile) {
+      e0 = next_event(c);
+      cudaEventRecord(e0, c->stream);
+    }
+  }
+  ~Phase() {
+    if (c->profile) {
+      cudaEvent_t e1 = next_event(c);
+      cudaEventRecord(e1, c->stream);
+      c->marks.push_back({id, {e0, e1}});
+    }
+  }
+};
+
+#define CHECK_ALLOC(expr)              \
+  do {                                 \
+    int _r = (expr);                   \
+    if (_r != HOTRG_OK) {              \
+      c->poisoned = _r;                \
+      return _r;                       \
+    }                                  \
+  } while (0)
+
+int cuda_status(hotrg_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "hotrg: CUDA error %s\n", cudaGetErrorString(e));
+    c->poisoned = HOTRG_ECUDA;
+    return HOTRG_ECUDA;
+  }
+  return HOTRG_OK;
+}
+
+// strides of the slot layout for bond dims per slot
+void slot_strides(int d, const int* slot_chi, long long* row_stride, long long* col_stride,
+                  long long* R) {
+  long long r = 1;
+  for (int s = 0; s < d; ++s) r *= slot_chi[s];
+  *R = r;
+  long long st = 1;
+  for (int s = d - 1; s >= 0; --s) {
+    col_stride[s] = st;
+    row_stride[s] = st * r;
+    st *= slot_chi[s];
+  }
+}
+
+// Permute T (slot layout with `from` order) into slot layout with `to` order.
+void permute_slots(hotrg_ctx* c, const double* in, const int* from, double* out, const int* to,
+                   double scale) {
+  int d = c->d;
+  int chi_from[kMaxD], chi_to[kMaxD];
+  for (int s = 0; s < d; ++s) {
+    chi_from[s] = c->chis[from[s]];
+    chi_to[s] = c->chis[to[s]];
+  }
+  long long rs[kMaxD], cs[kMaxD], R;
+  slot_strides(d, chi_from, rs, cs, &R);
+  long long size[kMaxDims], ist[kMaxDims];
+  for (int s = 0; s < d; ++s) {
+    int src = 0;
+    for (int t = 0; t < d; ++t)
+      if (from[t] == to[s]) src = t;
+    size[s] = chi_to[s];
+    ist[s] = rs[src];
+    size[d + s] = chi_to[s];
+    ist[d + s] = cs[src];
+  }
+  launch_permute(in, out, 2 * d, size, ist, scale, c->stream);
+}
+
+// interchange layout (x_0, x_0', x_1, x_1', ...) <-> slot layout
+void interchange_to_slots(hotrg_ctx* c, const double* in, double* out) {
+  int d = c->d;
+  // input strides of the interchange layout
+  long long st[2 * kMaxD];
+  long long acc = 1;
+  for (int k = 2 * d - 1; k >= 0; --k) {
+    st[k] = acc;
+    acc *= c->chis[k / 2];
+  }
+  long long size[kMaxDims], ist[kMaxDims];
+  for (int s = 0; s < d; ++s) {
+    int ax = c->order[s];
+    size[s] = c->chis[ax];
+    ist[s] = st[2 * ax];
+    size[d + s] = c->chis[ax];
+    ist[d + s] = st[2 * ax + 1];
+  }
+  launch_permute(in, out, 2 * d, size, ist, 1.0, c->stream);
+}
+
+void slots_to_interchange(hotrg_ctx* c, const double* in, double* out) {
+  int d = c->d;
+  int slot_chi[kMaxD];
+  for (int s = 0; s < d; ++s) slot_chi[s] = c->chis[c->order[s]];
+  long long rs[kMaxD], cs[kMaxD], R;
+  slot_strides(d, slot_chi, rs, cs, &R);
+  long long size[kMaxDims], ist[kMaxDims];
+  for (int k = 0; k < d; ++k) {
+    int s = 0;
+    for (int t = 0; t < d; ++t)
+      if (c->order[t] == k) s = t;
+    size[2 * k] = c->chis[k];
+    ist[2 * k] = rs[s];
+    size[2 * k + 1] = c->chis[k];
+    ist[2 * k + 1] = cs[s];
+  }
+  launch_permute(in, out, 2 * d, size, ist, 1.0, c->stream);
+}
+
+long long tensor_elems(hotrg_ctx* c) {
+  long long n = 1;
+  for (int k = 0; k < c->d; ++k) n *= (long long)c->chis[k] * c->chis[k];
+  return n;
+}
+
+// Trace, Y, X and the ln Z bookkeeping of the tensor in c->T (slot layout),
+// then normalisation of c->T in place (Secs. 4.2.1 / 4.2.11-4.2.16).
+void trace_and_normalise(hotrg_ctx* c, double* Tsrc, int first) {
+  int d = c->d;
+  int chi_c = c->chis[c->order[0]];
+  long long pn = 1;
+  for (int s = 1; s < d; ++s) pn *= c->chis[c->order[s]];
+  DevState* st = (DevState*)c->state.p;
+  launch_trace_y(Tsrc, chi_c, pn, (double*)c->Y.p, c->stream);
+  launch_finish_step((double*)c->Y.p, chi_c, st, c->p, first, c->stream);
+  launch_scale(Tsrc, (double*)c->T.p, tensor_elems(c), st, c->stream);
+}
+
+int start_run(hotrg_ctx* c) {
+  CHECK_ALLOC(dev_alloc(c, c->state, sizeof(DevState)));
+  CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
+  cudaMemsetAsync(c->state.p, 0, sizeof(DevState), c->stream);
+  trace_and_normalise(c, (double*)c->T.p, 1);
+  return cuda_status(c);
+}
+
+int sync_and_status(hotrg_ctx* c, DevState* out) {
+  if (c->poisoned) return HOTRG_ESTATE;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    c->poisoned = HOTRG_ECUDA;
+    return HOTRG_ECUDA;
+  }
+  DevState st;
+  if (cudaMemcpy(&st, c->state.p, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    c->poisoned = HOTRG_ECUDA;
+    return HOTRG_ECUDA;
+  }
+  if (st.status != 0) {
+    c->poisoned = st.status;
+    return st.status;
+  }
+  if (out) *out = st;
+  return HOTRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hotrg_strerror(int status) {
+  switch (status) {
+    case HOTRG_OK: return "ok";
+    case HOTRG_EINVAL: return "invalid argument";
+    case HOTRG_ENOMEM: return "device allocation failed";
+    case HOTRG_ECUDA: return "CUDA call failed";
+    case HOTRG_ENUMERIC: return "trace of the new tensor is not positive and finite";
+    case HOTRG_ENOTCONV: return "Jacobi eigen-solver hit its sweep cap";
+    case HOTRG_ETIMEOUT: return "bounded device wait expired";
+    case HOTRG_ESTATE: return "context unusable (earlier failure) or no step yet";
+    default: return "unknown status";
+  }
+}
+
+int hotrg_init_ising(int d, double beta, double h, hotrg_ctx** out) {
+  if (!out || d < 2 || d > kMaxD || !(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
+    return HOTRG_EINVAL;
+  *out = nullptr;
+  hotrg_ctx* c = new hotrg_ctx();
+  c->d = d;
+  c->beta = beta;
+  for (int k = 0; k < d; ++k) {
+    c->chis[k] = 2;
+    c->order[k] = k;
+  }
+  int r = dev_alloc(c, c->T, sizeof(double) << (2 * d));
+  if (r == HOTRG_OK) {
+    launch_init_ising((double*)c->T.p, d, beta, h, c->stream);
+    r = start_run(c);
+  }
+  if (r != HOTRG_OK) {
+    hotrg_free(c);
+    return r;
+  }
+  *out = c;
+  return HOTRG_OK;
+}
+
+int hotrg_init_tensor(int d, const int* chis, const double* T, double beta, hotrg_ctx** out) {
+  if (!out || !chis || !T || d < 2 || d > kMaxD || !(beta >= 0.0)) return HOTRG_EINVAL;
+  for (int k = 0; k < d; ++k)
+    if (chis[k] < 1 || chis[k] > 32) return HOTRG_EINVAL;
+  *out = nullptr;
+  hotrg_ctx* c = new hotrg_ctx();
+  c->d = d;
+  c->beta = beta;
+  for (int k = 0; k < d; ++k) {
+    c->chis[k] = chis[k];
+    c->order[k] = k;
+  }
+  size_t bytes = sizeof(double) * tensor_elems(c);
+  int r = dev_alloc(c, c->T, bytes);
+  if (r == HOTRG_OK) r = dev_alloc(c, c->Xp, bytes);
+  if (r == HOTRG_OK) {
+    if (cudaMemcpyAsync(c->Xp.p, T, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess) r = HOTRG_ECUDA;
+  }
+  if (r == HOTRG_OK) {
+    interchange_to_slots(c, (const double*)c->Xp.p, (double*)c->T.p);
+    r = start_run(c);
+  }
+  if (r != HOTRG_OK) {
+    cudaGetLastError();
+    hotrg_free(c);
+    return r;
+  }
+  *out = c;
+  return HOTRG_OK;
+}
+
+int hotrg_set_tensor(hotrg_ctx* c, const int* chis, const double* T) {
+  if (!c || !chis || !T) return HOTRG_EINVAL;
+  if (c->poisoned) return HOTRG_ESTATE;
+  for (int k = 0; k < c->d; ++k)
+    if (chis[k] < 1 || chis[k] > 32) return HOTRG_EINVAL;
+  for (int k = 0; k < c->d; ++k) {
+    c->chis[k] = chis[k];
+    c->order[k] = k;
+  }
+  size_t bytes = sizeof(double) * tensor_elems(c);
+  CHECK_ALLOC(dev_alloc(c, c->T, bytes));
+  CHECK_ALLOC(dev_alloc(c, c->Xp, bytes));
+  if (cudaMemcpyAsync(c->Xp.p, T, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
+    return cuda_status(c);
+  interchange_to_slots(c, (const double*)c->Xp.p, (double*)c->T.p);
+  c->last_valid = 0;
+  int r = cuda_status(c);
+  if (r != HOTRG_OK) return r;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
+  return HOTRG_OK;
+}
+
+int hotrg_set_stream(hotrg_ctx* c, void* stream) {
+  if (!c) return HOTRG_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
+  c->stream = (cudaStream_t)stream;
+  return HOTRG_OK;
+}
+
+int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_fn, void* user) {
+  if (!c || (!alloc) != (!free_fn)) return HOTRG_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
+  // keep the tensor and the run state, drop every workspace
+  Buf keep[2] = {c->T, c->state};
+  size_t keep_bytes[2] = {c->T.bytes, c->state.bytes};
+  std::vector<char> host[2];
+  for (int i = 0; i < 2; ++i) {
+    host[i].resize(keep_bytes[i]);
+    if (keep[i].p && cudaMemcpy(host[i].data(), keep[i].p, keep_bytes[i], cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_status(c);
+  }
+  int n = 0;
+  Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
+              &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
+              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB};
+  n = (int)(sizeof(b) / sizeof(b[0]));
+  for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
+  c->afn = alloc;
+  c->ffn = free_fn;
+  c->user = user;
+  c->last_valid = 0;
+  Buf* kb[2] = {&c->T, &c->state};
+  for (int i = 0; i < 2; ++i) {
+    if (!keep_bytes[i]) continue;
+    CHECK_ALLOC(dev_alloc(c, *kb[i], keep_bytes[i]));
+    if (cudaMemcpy(kb[i]->p, host[i].data(), keep_bytes[i], cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_status(c);
+  }
+  CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
+  return HOTRG_OK;
+}
+
+int hotrg_set_precision(hotrg_ctx* c, int mode) {
+  if (!c || mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6) return HOTRG_EINVAL;
+  if (mode != HOTRG_PREC_FP64 && !tc_gemm_ready()) return HOTRG_ECUDA;
+  c->precision = mode;
+  return HOTRG_OK;
+}
+
+int hotrg_step(hotrg_ctx* c, int axis, int chi) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->poisoned) return HOTRG_ESTATE;
+  const int d = c->d;
+  if (axis < 0 || axis >= d || chi < 1 || chi > 32) return HOTRG_EINVAL;
+  cudaStream_t s = c->stream;
+
+  // ---- slot order for this step: Current = axis, Next j = (axis + j) mod d
+  int to[kMaxD];
+  for (int k = 0; k < d; ++k) to[k] = (axis + k) % d;
+  const int chi_c = c->chis[axis];
+  int chij[kMaxD], nnew[kMaxD];
+  long long P = 1, Pn = 1;
+  for (int j = 1; j < d; ++j) {
+    chij[j] = c->chis[to[j]];
+    nnew[j] = std::min(chij[j] * chij[j], chi);
+    P *= chij[j];
+    Pn *= nnew[j];
+  }
+  const long long R = (long long)chi_c * P;      // rows = cols of T
+  const long long Rn = (long long)chi_c * Pn;    // rows = cols of T'
+  const long long RR = R * R;
+  // bottleneck work of this step: 2 * R^2 * (P_new P) per c'-slice, chi_c slices
+  const double bn_flops = 2.0 * (double)R * (double)R * (double)Pn * (double)P * (double)chi_c;
+  const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below;
+  c->last_fp64 = fp64 ? 1 : 0;
+
+  c->marks.clear();
+  c->event_next = 0;
+  CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * RR));
+  CHECK_ALLOC(dev_alloc(c, c->Xp, sizeof(double) * RR));
+  bool same = true;
+  for (int k = 0; k < d; ++k) same = same && (c->order[k] == to[k]);
+  double* Tc = (double*)c->T.p;
+  if (!same) {
+    Phase ph(c, 0);
+    permute_slots(c, (const double*)c->T.p, c->order, (double*)c->T2.p, to, 1.0);
+    std::swap(c->T, c->T2);
+    Tc = (double*)c->T.p;
+    for (int k = 0; k < d; ++k) c->order[k] = to[k];
+  }
+
+  // strides of T in slot layout
+  long long rs[kMaxD], cs[kMaxD], Rchk;
+  {
+    int sc[kMaxD];
+    for (int k = 0; k < d; ++k) sc[k] = c->chis[to[k]];
+    slot_strides(d, sc, rs, cs, &Rchk);
+  }
+
+  // ---- environments (Sec. 3.2; Sec. 4.2.4), FP64
+  // legs grouped by n = chi_j^2 so that one Jacobi launch covers a group
+  const int nlegs = d - 1;
+  int grp_of[kMaxD], grp_n[kMaxD], grp_first_mat[kMaxD], ngrp = 0, mat_of_leg[kMaxD];
+  {
+    int nmat_acc = 0;
+    for (int j = 1; j < d; ++j) {
+      int n = chij[j] * chij[j];
+      int g = -1;
+      for (int q = 0; q < ngrp; ++q)
+        if (grp_n[q] == n) g = q;
+      if (g < 0) {
+        g = ngrp++;
+        grp_n[g] = n;
+      }
+      grp_of[j] = g;
+    }
+    // matrices laid out group by group, two per leg (A, A')
+    for (int g = 0; g < ngrp; ++g) {
+      grp_first_mat[g] = nmat_acc;
+      for (int j = 1; j < d; ++j)
+        if (grp_of[j] == g) {
+          mat_of_leg[j] = nmat_acc;
+          nmat_acc += 2;
+        }
+    }
+  }
+  // matrix element offsets: group base + local index * n^2
+  long long mat_elem_off[2 * kMaxD];
+  long long total_mat_elems = 0;
+  {
+    for (int g = 0; g < ngrp; ++g) {
+      int cnt = 0;
+      for (int j = 1; j < d; ++j)
+        if (grp_of[j] == g) cnt += 2;
+      for (int j = 1; j < d; ++j)
+        if (grp_of[j] == g) {
+          int local = mat_of_leg[j] - grp_first_mat[g];
+          mat_elem_off[2 * j] = total_mat_elems + (long long)local * grp_n[g] * grp_n[g];
+          mat_elem_off[2 * j + 1] = mat_elem_off[2 * j] + (long long)grp_n[g] * grp_n[g];
+        }
+      total_mat_elems += (long long)cnt * grp_n[g] * grp_n[g];
+    }
+  }
+  long long mmax = 0, nmax = 0;
+  for (int j = 1; j < d; ++j) {
+    mmax = std::max<long long>(mmax, (long long)chij[j] * chi_c);
+    nmax = std::max<long long>(nmax, (long long)chij[j] * chij[j]);
+  }
+  const int nsplit_max = 64;
+  CHECK_ALLOC(dev_alloc(c, c->parts, sizeof(double) * nsplit_max * mmax * mmax));
+  CHECK_ALLOC(dev_alloc(c, c->S, sizeof(double) * 4 * nlegs * mmax * mmax));
+  CHECK_ALLOC(dev_alloc(c, c->Amat, sizeof(double) * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->W, sizeof(double) * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->V, sizeof(double) * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * 3 * 2 * kMaxD));
+  CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 2 * kMaxD));
+
+  for (int j = 1; j < d; ++j) {
+    Phase ph(c, 1);
+    const long long m = (long long)chij[j] * chi_c;
+    const long long K = RR / m;
+    for (int kind = 0; kind < 4; ++kind) {
+      // kind 0: S^  free (n_j, c');  1: S~  free (n_j, c);
+      // kind 2: S^' free (n'_j, c'); 3: S~' free (n'_j, c)
+      const int fpos = (kind < 2) ? j : d + j;
+      const int cpos = (kind == 0 || kind == 2) ? d : 0;
+      long long size[kMaxDims], ist[kMaxDims];
+      int nd = 0;
+      size[nd] = chij[j];
+      ist[nd++] = fpos < d ? rs[fpos] : cs[fpos - d];
+      size[nd] = chi_c;
+      ist[nd++] = cpos < d ? rs[cpos] : cs[cpos - d];
+      for (int q = 0; q < 2 * d; ++q) {
+        if (q == fpos || q == cpos) continue;
+        size[nd] = q < d ? c->chis[to[q]] : c->chis[to[q - d]];
+        ist[nd++] = q < d ? rs[q] : cs[q - d];
+      }
+      launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
+      int tiles = (int)((m + 63) / 64);
+      int upper_tiles = tiles * (tiles + 1) / 2;
+      int nsplit = std::max(1, std::min<int>(nsplit_max, (2 * 152 + upper_tiles - 1) / upper_tiles));
+      nsplit = (int)std::min<long long>(nsplit, std::max<long long>(1, K / 64));
+      launch_gemm_nt_f64((const double*)c->Xp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p,
+                         m, m * m, (int)m, (int)m, K, nsplit, 1, s);
+      // the GEMM may round nsplit down; recompute the same way
+      long long kchunk = (K + nsplit - 1) / nsplit;
+      kchunk = (kchunk + 15) / 16 * 16;
+      int used = (int)((K + kchunk - 1) / kchunk);
+      double* Sdst = (double*)c->S.p + ((long long)(j - 1) * 4 + kind) * mmax * mmax;
+      launch_reduce_sym((const double*)c->parts.p, used, (int)m, Sdst, s);
+    }
+    double* S0 = (double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
+    launch_assemble_a(S0, S0 + mmax * mmax, chij[j], chi_c, (double*)c->Amat.p + mat_elem_off[2 * j], s);
+    launch_assemble_a(S0 + 2 * mmax * mmax, S0 + 3 * mmax * mmax, chij[j], chi_c,
+                      (double*)c->Amat.p + mat_elem_off[2 * j + 1], s);
+  }
+
+  // ---- eigen-decomposition (Sec. 4.2.5), batched per group
+  for (int g = 0; g < ngrp; ++g) {
+    Phase ph(c, 2);
+    int cnt = 0;
+    long long base = -1;
+    for (int j = 1; j < d; ++j)
+      if (grp_of[j] == g) {
+        cnt += 2;
+        if (base < 0 || mat_elem_off[2 * j] < base) base = mat_elem_off[2 * j];
+      }
+    if (launch_jacobi((double*)c->W.p + base, (double*)c->V.p + base, (const double*)c->Amat.p + base,
+                      grp_n[g], cnt, 60, (int*)c->counters.p, (int*)c->sweeps.p,
+                      (DevState*)c->state.p, s) != 0)
+      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+  }
+
+  // ---- choice, truncation, gauge (Secs. 4.2.6-4.2.8)
+  long long lam_total = 0, u_total = 0;
+  long long lam_off[kMaxD], u_off[kMaxD];
+  for (int j = 1; j < d; ++j) {
+    lam_off[j] = lam_total;
+    lam_total += 2LL * chij[j] * chij[j];
+    u_off[j] = u_total;
+    u_total += (long long)chij[j] * chij[j] * nnew[j];
+  }
+  CHECK_ALLOC(dev_alloc(c, c->lam, sizeof(double) * lam_total));
+  CHECK_ALLOC(dev_alloc(c, c->U64, sizeof(double) * u_total));
+  CHECK_ALLOC(dev_alloc(c, c->U32, sizeof(float) * u_total));
+  CHECK_ALLOC(dev_alloc(c, c->legres, sizeof(LegResult) * kMaxD));
+  for (int j = 1; j < d; ++j) {
+    Phase ph(c, 3);
+    int n = chij[j] * chij[j];
+    // select_kernel addresses matrices 2*leg_index, 2*leg_index+1 from a base
+    launch_select((const double*)c->W.p + mat_elem_off[2 * j], (const double*)c->V.p + mat_elem_off[2 * j],
+                  n, 0, nnew[j], (double*)c->lam.p + lam_off[j], (double*)c->U64.p + u_off[j],
+                  (float*)c->U32.p + u_off[j], (LegResult*)c->legres.p + j, nullptr, s);
+  }
+
+  // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
+  const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
+  const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
+  const long long Kpad = fp64 ? R : (R + 63) / 64 * 64;
+  // chain intermediates
+  long long chain_max = 1;
+  {
+    long long acc = 1;
+    for (int j = 1; j < d - 1; ++j) {
+      acc *= nnew[j];
+      chain_max = std::max(chain_max, acc * chi_c * P * P);
+    }
+    for (int j = d - 1; j > 1; --j) {
+      long long hat = 1;
+      for (int k = 1; k < j; ++k) hat *= chij[k];
+      long long nn_tail = 1;
+      for (int k = j; k < d; ++k) nn_tail *= nnew[k];
+      chain_max = std::max(chain_max, (long long)chi_c * hat * Pn * hat * nn_tail);
+    }
+  }
+  size_t elt = (fp64 || c->f64_chains) ? sizeof(double) : sizeof(float);
+  CHECK_ALLOC(dev_alloc(c, c->chA, elt * chain_max));
+  CHECK_ALLOC(dev_alloc(c, c->chB, elt * chain_max));
+  if (fp64) {
+    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Ns * R));
+    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(double) * R * Ns));
+  } else {
+    CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
+    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Ns * Kpad));
+    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Ns));
+    if (Kpad != R) {
+      cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
+      cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Ns * Kpad, s);
+    }
+    Phase ph(c, 4);
+    launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
+  }
+  CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
+  double* Tn = (double*)c->T2.p;
+
+  // products of trailing bond sizes
+  auto prod_after = [&](const int* arr, int k) {
+    long long p_ = 1;
+    for (int l = k + 1; l < d; ++l) p_ *= arr[l];
+    return p_;
+  };
+  int terms_a[6], terms_b[6], nterms;
+  if (npieces == 2) {
+    int ta[3] = {1, 0, 0}, tb[3] = {0, 1, 0};
+    nterms = 3;
+    for (int t = 0; t < 3; ++t) {
+      terms_a[t] = ta[t];
+      terms_b[t] = tb[t];
+    }
+  } else {
+    int ta[6] = {2, 1, 0, 1, 0, 0}, tb[6] = {0, 1, 2, 0, 1, 0};
+    nterms = 6;
+    for (int t = 0; t < 6; ++t) {
+      terms_a[t] = ta[t];
+      terms_b[t] = tb[t];
+    }
+  }
+
+  for (int sl = 0; sl < chi_c; ++sl) {
+    // -- prime-side chain, Eqs. (TU1)-(TUNCD), on the c'-fixed tensor T[(rho, n~), (sl, n~')]
+    View in;
+    in.push_back({I_RHO, chi_c, rs[0]});
+    for (int k = 1; k < d; ++k) in.push_back({I_NC + k, chij[k], rs[k]});
+    for (int k = 1; k < d; ++k) in.push_back({I_NCP + k, chij[k], cs[k]});
+    const void* src = Tc + (long long)sl * cs[0];
+    int src_f64 = 1;
+    for (int j = 1; j < d; ++j) {
+      Phase ph(c, 5);
+      View out;
+      bool last = (j == d - 1);
+      if (!last) {
+        std::vector<std::pair<int, long long>> names;
+        for (int k = 1; k <= j; ++k) names.push_back({I_NP + k, nnew[k]});
+        names.push_back({I_RHO, chi_c});
+        for (int k = 1; k < d; ++k) names.push_back({I_NC + k, chij[k]});
+        for (int k = j + 1; k < d; ++k) names.push_back({I_NCP + k, chij[k]});
+        for (int k = 1; k <= j; ++k) names.push_back({I_NHP + k, chij[k]});
+        out = contiguous(names);
+      } else {
+        long long K_ = Kpad;
+        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nnew[k], prod_after(nnew, k) * P * K_});
+        for (int k = 1; k < d; ++k) out.push_back({I_NC + k, chij[k], prod_after(chij, k) * K_});
+        out.push_back({I_RHO, chi_c, P});
+        for (int k = 1; k < d; ++k) out.push_back({I_NHP + k, chij[k], prod_after(chij, k)});
+      }
+      ChainDesc cd = make_stage(in, out, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nnew[j]);
+      void* dst = last ? c->Bp.p : ((j & 1) ? c->chA.p : c->chB.p);
+      if (fp64) {
+        launch_chain_f64(cd, (const double*)src, (const double*)c->U64.p + u_off[j], (double*)dst, s);
+      } else if (c->f64_chains) {
+        cd.npieces = npieces;
+        cd.piece_stride = Ns * Kpad;
+        launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j], dst,
+                            last ? OUT_BF16_SPLIT : OUT_F64, s);
+      } else {
+        cd.npieces = npieces;
+        cd.piece_stride = Ns * Kpad;
+        launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j], dst,
+                         last ? OUT_BF16_SPLIT : OUT_F32, s);
+      }
+      src = dst;
+      src_f64 = (fp64 || c->f64_chains) ? 1 : 0;
+      in = out;
+    }
+    // -- bottleneck, Eq. (BottleneckPart): C[(c, n^)][(n', n~)] = T . B^T
+    {
+    Phase ph(c, 6);
+    if (fp64) {
+      launch_gemm_nt_f64(Tc, R, (const double*)c->Bp.p, R, (double*)c->Cb.p, Ns, 0, (int)R, (int)Ns,
+                         R, 1, 0, s);
+    } else {
+      if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Ns,
+                         (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Ns,
+                         &((DevState*)c->state.p)->status, s, nullptr) != 0)
+        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    }
+    }
+    // -- non-prime chain, Eqs. (AfterBNNCD)-(AfterBN1), Eq. (Elements_NewTensor)
+    View cin;
+    cin.push_back({I_C, chi_c, P * Ns});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NH + k, chij[k], prod_after(chij, k) * Ns});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nnew[k], prod_after(nnew, k) * P});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
+    const void* csrc = c->Cb.p;
+    for (int j = d - 1; j >= 1; --j) {
+      Phase ph(c, 7);
+      View out;
+      bool last = (j == 1);
+      if (!last) {
+        std::vector<std::pair<int, long long>> names;
+        names.push_back({I_C, chi_c});
+        for (int k = 1; k < j; ++k) names.push_back({I_NH + k, chij[k]});
+        for (int k = 1; k < d; ++k) names.push_back({I_NP + k, nnew[k]});
+        for (int k = 1; k < j; ++k) names.push_back({I_NC + k, chij[k]});
+        for (int k = j; k < d; ++k) names.push_back({I_N + k, nnew[k]});
+        out = contiguous(names);
+      } else {
+        out.push_back({I_C, chi_c, Pn * Rn});
+        for (int k = 1; k < d; ++k) out.push_back({I_N + k, nnew[k], prod_after(nnew, k) * Rn});
+        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nnew[k], prod_after(nnew, k)});
+      }
+      ChainDesc cd = make_stage(cin, out, I_NH + j, I_NC + j, I_N + j, chij[j], nnew[j]);
+      void* dst = last ? (void*)(Tn + (long long)sl * Pn) : ((j & 1) ? c->chA.p : c->chB.p);
+      if (fp64) {
+        launch_chain_f64(cd, (const double*)csrc, (const double*)c->U64.p + u_off[j], (double*)dst, s);
+      } else if (c->f64_chains) {
+        launch_chain_f64acc(cd, csrc, j == d - 1 ? 0 : 1, (const double*)c->U64.p + u_off[j], dst, OUT_F64, s);
+      } else {
+        launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
+      }
+      csrc = dst;
+      cin = out;
+    }
+  }
+
+  // ---- bond dims of the new tensor (Sec. 4.2.15 with the axes kept physical)
+  for (int j = 1; j < d; ++j) c->chis[to[j]] = nnew[j];
+  c->p += 1;
+  // ---- trace, Y, ratio X, ln Z, normalisation (Secs. 4.2.11-4.2.16)
+  CHECK_ALLOC(dev_alloc(c, c->T, sizeof(double) * Rn * Rn));
+  {
+    Phase ph(c, 8);
+    trace_and_normalise(c, Tn, 0);
+  }
+
+  c->last_valid = 1;
+  c->last_nlegs = nlegs;
+  for (int j = 1; j < d; ++j) {
+    c->last_leg_axis[j - 1] = to[j];
+    c->last_leg_n[j - 1] = chij[j] * chij[j];
+    c->last_leg_nnew[j - 1] = nnew[j];
+    c->last_lam_off[j - 1] = lam_off[j];
+    c->last_u_off[j - 1] = u_off[j];
+  }
+  return cuda_status(c);
+}
+
+static int find_leg(hotrg_ctx* c, int leg) {
+  if (!c->last_valid) return -1;
+  for (int j = 0; j < c->last_nlegs; ++j)
+    if (c->last_leg_axis[j] == leg) return j;
+  return -1;
+}
+
+int hotrg_isometry(hotrg_ctx* c, int leg, double* U, int64_t cap, int* rows, int* cols,
+                   int* chosen_prime) {
+  if (!c) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  int j = find_leg(c, leg);
+  if (j < 0) return c->last_valid ? HOTRG_EINVAL : HOTRG_ESTATE;
+  int n = c->last_leg_n[j], nn = c->last_leg_nnew[j];
+  if (rows) *rows = n;
+  if (cols) *cols = nn;
+  LegResult lr;
+  if (cudaMemcpy(&lr, (LegResult*)c->legres.p + (j + 1), sizeof(lr), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_status(c);
+  if (chosen_prime) *chosen_prime = lr.chose_prime;
+  if (!U || cap < (int64_t)n * nn) return HOTRG_EINVAL;
+  if (cudaMemcpy(U, (double*)c->U64.p + c->last_u_off[j], sizeof(double) * n * nn, cudaMemcpyDefault) != cudaSuccess)
+    return cuda_status(c);
+  return HOTRG_OK;
+}
+
+int hotrg_spectrum(hotrg_ctx* c, int leg, int prime, double* lam, int64_t cap, int* n_out) {
+  if (!c || (prime != 0 && prime != 1)) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  int j = find_leg(c, leg);
+  if (j < 0) return c->last_valid ? HOTRG_EINVAL : HOTRG_ESTATE;
+  int n = c->last_leg_n[j];
+  if (n_out) *n_out = n;
+  if (!lam || cap < n) return HOTRG_EINVAL;
+  if (cudaMemcpy(lam, (double*)c->lam.p + c->last_lam_off[j] + (long long)prime * n, sizeof(double) * n,
+                 cudaMemcpyDefault) != cudaSuccess)
+    return cuda_status(c);
+  return HOTRG_OK;
+}
+
+int hotrg_truncation(hotrg_ctx* c, int leg, double* eps, double* eps_prime) {
+  if (!c) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  int j = find_leg(c, leg);
+  if (j < 0) return c->last_valid ? HOTRG_EINVAL : HOTRG_ESTATE;
+  LegResult lr;
+  if (cudaMemcpy(&lr, (LegResult*)c->legres.p + (j + 1), sizeof(lr), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_status(c);
+  if (eps) *eps = lr.eps[0];
+  if (eps_prime) *eps_prime = lr.eps[1];
+  return HOTRG_OK;
+}
+
+int hotrg_free_energy(hotrg_ctx* c, double* lnZ_per_site, double* f_per_site) {
+  if (!c) return HOTRG_EINVAL;
+  DevState st;
+  int r = sync_and_status(c, &st);
+  if (r != HOTRG_OK) return r;
+  if (lnZ_per_site) *lnZ_per_site = st.ln_z_site;
+  if (f_per_site) *f_per_site = c->beta > 0 ? -st.ln_z_site / c->beta : NAN;
+  return HOTRG_OK;
+}
+
+int hotrg_observables(hotrg_ctx* c, double* trace, double* gu_wen_X, int* nsteps) {
+  if (!c) return HOTRG_EINVAL;
+  DevState st;
+  int r = sync_and_status(c, &st);
+  if (r != HOTRG_OK) return r;
+  if (trace) *trace = st.trace;
+  if (gu_wen_X) *gu_wen_X = st.gu_wen;
+  if (nsteps) *nsteps = c->p;
+  return HOTRG_OK;
+}
+
+int hotrg_bond_dims(hotrg_ctx* c, int dims[4]) {
+  if (!c || !dims) return HOTRG_EINVAL;
+  for (int k = 0; k < 4; ++k) dims[k] = k < c->d ? c->chis[k] : 0;
+  return HOTRG_OK;
+}
+
+int hotrg_tensor(hotrg_ctx* c, double* T, int64_t cap, int dims[8]) {
+  if (!c) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  long long n = tensor_elems(c);
+  if (dims)
+    for (int k = 0; k < 8; ++k) dims[k] = k < 2 * c->d ? c->chis[k / 2] : 0;
+  if (!T || cap < n) return HOTRG_EINVAL;
+  int ra = dev_alloc(c, c->Xp, sizeof(double) * n);
+  if (ra != HOTRG_OK) return ra;
+  slots_to_interchange(c, (const double*)c->T.p, (double*)c->Xp.p);
+  if (cudaMemcpyAsync(T, c->Xp.p, sizeof(double) * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+    return cuda_status(c);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
+  return cuda_status(c);
+}
+
+int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* B, double* C) {
+  if (mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6 || M < 1 || N < 1 || K < 1 ||
+      M > (1 << 20) || N > (1 << 20) || K > (1 << 20) || !A || !B || !C)
+    return HOTRG_EINVAL;
+  if ((long long)M * K > (1LL << 31) || (long long)N * K > (1LL << 31) || (long long)M * N > (1LL << 31))
+    return HOTRG_EINVAL;
+  if (mode != HOTRG_PREC_FP64 && !tc_gemm_ready()) return HOTRG_ECUDA;
+  cudaStream_t s = nullptr;
+  const int np = mode == HOTRG_PREC_BF16X3 ? 2 : 3;
+  const long long Kpad = mode == HOTRG_PREC_FP64 ? K : ((long long)K + 63) / 64 * 64;
+  void *dA = nullptr, *dB = nullptr, *dC = nullptr, *pA = nullptr, *pB = nullptr, *c32 = nullptr;
+  int* err = nullptr;
+  int status = HOTRG_OK;
+  auto fail = [&](int st) {
+    if (status == HOTRG_OK) status = st;
+  };
+  if (cudaMalloc(&dA, sizeof(double) * M * K) || cudaMalloc(&dB, sizeof(double) * N * K) ||
+      cudaMalloc(&dC, sizeof(double) * M * N) || cudaMalloc(&err, sizeof(int)))
+    fail(HOTRG_ENOMEM);
+  if (status == HOTRG_OK && mode != HOTRG_PREC_FP64) {
+    if (cudaMalloc(&pA, sizeof(__nv_bfloat16) * np * M * Kpad) ||
+        cudaMalloc(&pB, sizeof(__nv_bfloat16) * np * N * Kpad) || cudaMalloc(&c32, sizeof(float) * M * N))
+      fail(HOTRG_ENOMEM);
+  }
+  if (status == HOTRG_OK) {
+    cudaMemcpy(dA, A, sizeof(double) * M * K, cudaMemcpyDefault);
+    cudaMemcpy(dB, B, sizeof(double) * N * K, cudaMemcpyDefault);
+    cudaMemset(err, 0, sizeof(int));
+    if (mode == HOTRG_PREC_FP64) {
+      launch_gemm_nt_f64((const double*)dA, K, (const double*)dB, K, (double*)dC, N, 0, M, N, K, 1, 0, s);
+    } else {
+      cudaMemset(pA, 0, sizeof(__nv_bfloat16) * np * M * Kpad);
+      cudaMemset(pB, 0, sizeof(__nv_bfloat16) * np * N * Kpad);
+      launch_split_bf16((const double*)dA, M, K, K, (__nv_bfloat16*)pA, Kpad, M * Kpad, np, s);
+      launch_split_bf16((const double*)dB, N, K, K, (__nv_bfloat16*)pB, Kpad, N * Kpad, np, s);
+      int ta3[3] = {1, 0, 0}, tb3[3] = {0, 1, 0};
+      int ta6[6] = {2, 1, 0, 1, 0, 0}, tb6[6] = {0, 1, 2, 0, 1, 0};
+      if (launch_tc_gemm((const __nv_bfloat16*)pA, M, (const __nv_bfloat16*)pB, N, (int)Kpad, np,
+                         np == 2 ? 3 : 6, np == 2 ? ta3 : ta6, np == 2 ? tb3 : tb6, (float*)c32, N, err,
+                         s, nullptr) != 0)
+        fail(HOTRG_ECUDA);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) fail(HOTRG_ECUDA);
+    int e = 0;
+    cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e) fail(e);
+    if (status == HOTRG_OK) {
+      if (mode == HOTRG_PREC_FP64) {
+        cudaMemcpy(C, dC, sizeof(double) * M * N, cudaMemcpyDefault);
+      } else {
+        std::vector<float> h((size_t)M * N);
+        cudaMemcpy(h.data(), c32, sizeof(float) * M * N, cudaMemcpyDeviceToHost);
+        std::vector<double> hd(h.begin(), h.end());
+        cudaMemcpy(C, hd.data(), sizeof(double) * M * N, cudaMemcpyDefault);
+      }
+      if (cudaGetLastError() != cudaSuccess) fail(HOTRG_ECUDA);
+    }
+  }
+  cudaGetLastError();
+  for (void* p : {dA, dB, dC, pA, pB, c32, (void*)err})
+    if (p) cudaFree(p);
+  return status;
+}
+
+int hotrg_set_fp64_threshold(hotrg_ctx* c, double flops) {
+  if (!c || !(flops >= 0.0)) return HOTRG_EINVAL;
+  c->fp64_below = flops;
+  return HOTRG_OK;
+}
+
+int hotrg_profile(hotrg_ctx* c, int enable) {
+  if (!c) return HOTRG_EINVAL;
+  c->profile = enable ? 1 : 0;
+  return HOTRG_OK;
+}
+
+int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int* contraction_fp64) {
+  if (!c || !ms) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  for (int k = 0; k < 16; ++k) {
+    ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  for (auto& m : c->marks) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, m.second.first, m.second.second) != cudaSuccess) return cuda_status(c);
+    ms[m.first] += t;
+    if (launches) launches[m.first] += 1;
+  }
+  if (n) *n = 9;
+  if (contraction_fp64) *contraction_fp64 = c->last_fp64;
+  return HOTRG_OK;
+}
+
+int hotrg_device_bytes(hotrg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return HOTRG_EINVAL;
+  *bytes = c->held;
+  return HOTRG_OK;
+}
+
+int hotrg_launch_count(hotrg_ctx* c, int64_t* launches) {
+  if (!c || !launches) return HOTRG_EINVAL;
+  *launches = g_launches;
+  return HOTRG_OK;
+}
+
+void hotrg_free(hotrg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaGetLastError();
+  Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
+              &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
+              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB};
+  for (auto* x : b) dev_release(c, *x);
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

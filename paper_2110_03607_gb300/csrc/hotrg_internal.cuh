@@ -1,0 +1,99 @@
+// Internal declarations shared by the translation units of libhotrg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace hotrg {
+
+constexpr int kMaxD = 4;
+constexpr int kMaxDims = 8;      // tensor ranks handled by the index kernels
+constexpr int kMaxBond = 64;
+
+// Device-side state of a run; lives in device memory, read back on demand.
+struct DevState {
+  double kappa;        // K^(p) / 2^p
+  double ln_tr;        // ln Tr T^(p) of the last new tensor (or of T^(0))
+  double trace;        // Tr T^(p)
+  double inv_trace;    // f^(p) = 1 / Tr T^(p)
+  double ln_z_site;    // ln Z^(p) / 2^p
+  double gu_wen;       // X of the last new tensor
+  int status;          // 0 or a negative hotrg_status
+  int pad;
+};
+
+// Per-leg results of the isometry selection.
+struct LegResult {
+  double eps[2];       // epsilon (A), epsilon' (A')
+  double lam1[2];
+  double gap;
+  int chose_prime;
+  int sweeps[2];
+};
+
+// Generic strided description of a tensor-times-isometry stage: every
+// output element (over `ndim` free dims, plus the new index n) is
+//   y = sum_{a in A(o), b} x[in(o) + a*ka_stride + b*kb_stride] * U[a + b*chi][n]
+// with A(o) = {o[a_dim]} when a_dim >= 0 (the hat index stays free: prime
+// side) and A(o) = [0, chi) when a_dim < 0 (both contracted: non-prime side).
+struct ChainDesc {
+  int ndim;
+  int a_dim;
+  int chi;             // chi_j (U has chi*chi rows)
+  int nn;              // chi_j^new (U columns)
+  long long size[kMaxDims];
+  long long in_stride[kMaxDims];
+  long long out_stride[kMaxDims];
+  long long ka_stride, kb_stride;
+  long long n_out_stride;
+  long long total;     // product of size[]
+  long long piece_stride;  // split outputs: distance between BF16 pieces
+  int npieces;
+};
+
+// ---- kernels_tensor.cu
+void launch_init_ising(double* T, int d, double beta, double h, cudaStream_t s);
+void launch_permute(const double* in, double* out, int ndim, const long long* out_size,
+                    const long long* in_stride, double scale, cudaStream_t s);
+void launch_split_bf16(const double* in, long long rows, long long cols, long long ld_in,
+                       __nv_bfloat16* out, long long ld_out, long long piece_stride, int npieces,
+                       cudaStream_t s);
+void launch_trace_y(const double* Tn, int chi_c, long long pn, double* Y, cudaStream_t s);
+void launch_finish_step(double* Y, int chi_c, DevState* st, int p, int first, cudaStream_t s);
+void launch_scale(const double* in, double* out, long long n, const DevState* st, cudaStream_t s);
+
+// ---- kernels_env.cu
+void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb,
+                        double* C, long long ldc, long long split_stride,
+                        int M, int N, long long K, int nsplit, int upper_only, cudaStream_t s);
+void launch_reduce_sym(const double* parts, int nsplit, int m, double* G, cudaStream_t s);
+void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int chi_c,
+                       double* A, cudaStream_t s);
+
+// ---- kernels_eig.cu
+int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
+                  int* counters, int* sweeps_out, DevState* st, cudaStream_t s);
+void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
+                   double* lam_sorted, double* U64, float* U32, LegResult* res,
+                   int* scratch_order, cudaStream_t s);
+
+// ---- kernels_chain.cu
+void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U,
+                      void* out, int out_mode, cudaStream_t s);
+void launch_chain_f64(const ChainDesc& d, const double* in, const double* U, double* out,
+                      cudaStream_t s);
+void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, const double* U,
+                         void* out, int out_mode, cudaStream_t s);
+enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2 };
+
+// ---- kernels_tc_gemm.cu
+// C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T
+int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
+                   int npieces, int nterms, const int* pa, const int* pb,
+                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out);
+int tc_gemm_ready();
+int tc_chunk_kblocks();
+
+extern long long g_launches;
+}  // namespace hotrg

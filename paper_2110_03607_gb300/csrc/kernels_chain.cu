@@ -1,0 +1,150 @@
+// Tensor-times-isometry stages of the new-tensor contraction (Sec. 4.2.9):
+//  * prime side, Eqs. (TU1)-(TUNCD): sum over n-check'_j of
+//    U~^(j)_{(n^'_j n~'_j), n'_j} C~ -- the hat index n^'_j stays free;
+//  * non-prime side, Eqs. (AfterBNNCD)-(AfterBN1): sum over (n^_j, n~_j) of
+//    U~^(j)_{(n^_j n~_j), n_j} C^.
+// A stage is described by a ChainDesc (strides of every free index in the
+// input and output, strides of the contracted hat/check indices).  Each
+// thread owns one free multi-index and accumulates all chi_j^new outputs in
+// registers; U~^(j) sits in shared memory (rows padded by one word so that
+// lanes with different hat indices hit different banks).
+#include "hotrg_internal.cuh"
+
+namespace hotrg {
+
+template <typename TIn, typename TAcc, int NN, int OUT>
+__global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
+                                                    const TAcc* __restrict__ U, void* out) {
+  extern __shared__ __align__(16) unsigned char smem_u[];
+  TAcc* us = reinterpret_cast<TAcc*>(smem_u);
+  const int rows = d.chi * d.chi;
+  const int ld = NN + 1;
+  for (int e = threadIdx.x; e < rows * NN; e += blockDim.x) {
+    int r = e / NN, c = e % NN;
+    us[r * ld + c] = c < d.nn ? U[r * d.nn + c] : TAcc(0);
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.total; t += stride) {
+    long long rem = t, in_off = 0, out_off = 0;
+    int a_val = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxDims; ++k) {
+      if (k >= d.ndim) break;
+      long long sz = d.size[k];
+      long long q = rem / sz;
+      long long idx = rem - q * sz;
+      rem = q;
+      in_off += idx * d.in_stride[k];
+      out_off += idx * d.out_stride[k];
+      if (k == d.a_dim) a_val = (int)idx;
+    }
+    TAcc acc[NN];
+#pragma unroll
+    for (int n = 0; n < NN; ++n) acc[n] = TAcc(0);
+    const int a_lo = d.a_dim >= 0 ? a_val : 0;
+    const int a_hi = d.a_dim >= 0 ? a_val + 1 : d.chi;
+    if (d.a_dim >= 0) {
+      // prime side: one hat index, chi terms
+      const TIn* xa = in + in_off;
+      for (int b = 0; b < d.chi; ++b) {
+        TAcc x = (TAcc)xa[(long long)b * d.kb_stride];
+        const TAcc* ur = us + (a_val + b * d.chi) * ld;
+#pragma unroll
+        for (int n = 0; n < NN; ++n) acc[n] = fma(x, ur[n], acc[n]);
+      }
+    } else
+    // non-prime side, chi^2 terms, summed in two levels: the chi terms over b go
+    // into a fresh partial that is then added once (rounding ~2 sqrt(chi), not chi)
+    for (int a = a_lo; a < a_hi; ++a) {
+      const TIn* xa = in + in_off + (long long)a * d.ka_stride;
+      TAcc part[NN];
+#pragma unroll
+      for (int n = 0; n < NN; ++n) part[n] = TAcc(0);
+      for (int b = 0; b < d.chi; ++b) {
+        TAcc x = (TAcc)xa[(long long)b * d.kb_stride];
+        const TAcc* ur = us + (a + b * d.chi) * ld;
+#pragma unroll
+        for (int n = 0; n < NN; ++n) part[n] = fma(x, ur[n], part[n]);
+      }
+#pragma unroll
+      for (int n = 0; n < NN; ++n) acc[n] += part[n];
+    }
+    if (OUT == OUT_F32) {
+      float* o = (float*)out;
+#pragma unroll
+      for (int n = 0; n < NN; ++n)
+        if (n < d.nn) o[out_off + n * d.n_out_stride] = (float)acc[n];
+    } else if (OUT == OUT_F64) {
+      double* o = (double*)out;
+#pragma unroll
+      for (int n = 0; n < NN; ++n)
+        if (n < d.nn) o[out_off + n * d.n_out_stride] = (double)acc[n];
+    } else {
+      __nv_bfloat16* o = (__nv_bfloat16*)out;
+#pragma unroll
+      for (int n = 0; n < NN; ++n) {
+        if (n >= d.nn) break;
+        TAcc x = acc[n];
+        long long off = out_off + n * d.n_out_stride;
+        for (int p = 0; p < d.npieces; ++p) {
+          __nv_bfloat16 bv = __double2bfloat16((double)x);
+          o[off + p * d.piece_stride] = bv;
+          x -= (TAcc)__bfloat162float(bv);
+        }
+      }
+    }
+  }
+}
+
+template <typename TIn, typename TAcc, int NN, int OUT>
+static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, cudaStream_t s) {
+  size_t smem = (size_t)d.chi * d.chi * (NN + 1) * sizeof(TAcc);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  long long blocks = (d.total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  chain_kernel<TIn, TAcc, NN, OUT><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out);
+  ++g_launches;
+}
+
+template <typename TIn, typename TAcc, int NN>
+static void dispatch_out(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, int out_mode,
+                         cudaStream_t s) {
+  if (out_mode == OUT_F32) launch_one<TIn, TAcc, NN, OUT_F32>(d, in, U, out, s);
+  else if (out_mode == OUT_F64) launch_one<TIn, TAcc, NN, OUT_F64>(d, in, U, out, s);
+  else launch_one<TIn, TAcc, NN, OUT_BF16_SPLIT>(d, in, U, out, s);
+}
+
+template <typename TIn, typename TAcc>
+static void dispatch_nn(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, int out_mode,
+                        cudaStream_t s) {
+  if (d.nn <= 4) dispatch_out<TIn, TAcc, 4>(d, in, U, out, out_mode, s);
+  else if (d.nn <= 8) dispatch_out<TIn, TAcc, 8>(d, in, U, out, out_mode, s);
+  else if (d.nn <= 16) dispatch_out<TIn, TAcc, 16>(d, in, U, out, out_mode, s);
+  else if (d.nn <= 24) dispatch_out<TIn, TAcc, 24>(d, in, U, out, out_mode, s);
+  else dispatch_out<TIn, TAcc, 32>(d, in, U, out, out_mode, s);
+}
+
+void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U, void* out,
+                      int out_mode, cudaStream_t s) {
+  if (in_is_f64) dispatch_nn<double, float>(d, (const double*)in, U, out, out_mode, s);
+  else dispatch_nn<float, float>(d, (const float*)in, U, out, out_mode, s);
+}
+
+// FP64 accumulation: the FP64 form of the step (double in, double out), and the
+// FP64-chain variant of the split form (double or float in, any output).
+void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, const double* U, void* out,
+                         int out_mode, cudaStream_t s) {
+  if (in_is_f64) dispatch_nn<double, double>(d, (const double*)in, U, out, out_mode, s);
+  else dispatch_nn<float, double>(d, (const float*)in, U, out, out_mode, s);
+}
+
+void launch_chain_f64(const ChainDesc& d, const double* in, const double* U, double* out,
+                      cudaStream_t s) {
+  dispatch_nn<double, double>(d, in, U, out, OUT_F64, s);
+}
+
+}  // namespace hotrg

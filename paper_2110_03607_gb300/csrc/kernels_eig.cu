@@ -1,0 +1,295 @@
+// Batched FP64 one-sided (Hestenes) Jacobi eigen-solver for the symmetric
+// PSD environment matrices A^(j), A'^(j) (Sec. 4.2.5, Eqs. SVD_N / SVD_P),
+// and the choice / truncation / sign gauge of the isometries (Secs. 2,
+// 4.2.6-4.2.8).
+//
+// One-sided Jacobi: W = A V is orthogonalised column pair by column pair by
+// plane rotations applied to W and V; at convergence the columns of W are
+// mutually orthogonal, so V diagonalises A^T A = A^2 and, A being PSD,
+// A v_i = lambda_i v_i with lambda_i = ||w_i||.  Pairs follow the round-robin
+// ordering (n/2 disjoint pairs per round, n-1 rounds per sweep), so every
+// pair of a round -- over all matrices of the batch -- runs in parallel on
+// its own warp; rounds are separated by a grid-wide barrier of a cooperative
+// launch.  A pair whose inner product is exactly 0 is never rotated, which
+// keeps an exact Z2 block pattern of A exact.
+#include <cooperative_groups.h>
+
+#include "hotrg_internal.cuh"
+#include "../../include/hotrg.h"
+
+namespace cg = cooperative_groups;
+
+namespace hotrg {
+
+__device__ __forceinline__ int rr_slot(int i, int r, int mp) {
+  // circle method: player 0 fixed, the others rotate by r
+  return i == 0 ? 0 : 1 + (i - 1 + r) % (mp - 1);
+}
+
+// NPL = ceil(n / 32): column entries held per lane
+template <int NPL>
+__global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double* V,
+                                                               const double* __restrict__ A, int n,
+                                                               int nmat, int max_sweeps,
+                                                               int* counters, int* sweeps_out,
+                                                               DevState* st) {
+  cg::grid_group grid = cg::this_grid();
+  const long long nn = (long long)n * n;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gthreads = (long long)gridDim.x * blockDim.x;
+  for (long long e = gtid; e < (long long)nmat * nn; e += gthreads) {
+    long long r = e % nn;
+    int i = (int)(r / n), j = (int)(r % n);
+    __stcg(W + e, A[e]);                // A symmetric: row i = column i
+    __stcg(V + e, i == j ? 1.0 : 0.0);
+  }
+  if (gtid < 3 * nmat) counters[gtid] = 0;
+  grid.sync();
+
+  const int mp = n + (n & 1);
+  const int npairs = mp / 2;
+  const int rounds = mp - 1;
+  const int lane = threadIdx.x & 31;
+  // consecutive tasks go to different blocks (SMs), spreading the FP64 work
+  const int gw = (int)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int nw = (int)(gthreads >> 5);
+  const int ntasks = nmat * npairs;
+  // the computed inner product carries rounding of order n eps sqrt(a b): a
+  // tolerance below that level would keep rotating rounding noise forever
+  const double tol = 4.0 * (double)n * 2.220446049250313e-16;
+
+  int sweep = 1;
+  bool converged = false;
+  for (; sweep <= max_sweeps; ++sweep) {
+    int* cur = counters + (sweep % 3) * nmat;
+    if (blockIdx.x == 0 && (int)threadIdx.x < nmat) counters[((sweep + 1) % 3) * nmat + threadIdx.x] = 0;
+    for (int r = 0; r < rounds; ++r) {
+      for (int task = gw; task < ntasks; task += nw) {
+        int mat = task / npairs, k = task % npairs;
+        int p = rr_slot(k, r, mp), q = rr_slot(mp - 1 - k, r, mp);
+        if (p >= n || q >= n) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        double* wp = W + mat * nn + (long long)p * n;
+        double* wq = W + mat * nn + (long long)q * n;
+        double a = 0.0, b = 0.0, g = 0.0;
+        double xs[NPL], ys[NPL];
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          double x = i < n ? __ldcg(wp + i) : 0.0, y = i < n ? __ldcg(wq + i) : 0.0;
+          xs[u] = x;
+          ys[u] = y;
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        bool rot = (g != 0.0) && (fabs(g) > tol * sqrt(a * b));
+        if (!rot) continue;
+        double zeta = (b - a) / (2.0 * g);
+        double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = c * t;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          if (i < n) {
+            __stcg(wp + i, c * xs[u] - s * ys[u]);
+            __stcg(wq + i, s * xs[u] + c * ys[u]);
+          }
+        }
+        double* vp = V + mat * nn + (long long)p * n;
+        double* vq = V + mat * nn + (long long)q * n;
+        for (int i = lane; i < n; i += 32) {
+          double x = __ldcg(vp + i), y = __ldcg(vq + i);
+          __stcg(vp + i, c * x - s * y);
+          __stcg(vq + i, s * x + c * y);
+        }
+        if (lane == 0) atomicAdd(cur + mat, 1);
+      }
+      grid.sync();
+    }
+    int total = 0;
+    for (int m = 0; m < nmat; ++m) total += __ldcg(cur + m);
+    if (total == 0) {
+      converged = true;
+      break;
+    }
+  }
+  if (gtid == 0) {
+    for (int m = 0; m < nmat; ++m) sweeps_out[m] = sweep;
+    if (!converged && st->status == 0) st->status = HOTRG_ENOTCONV;
+  }
+}
+
+template <int NPL>
+static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
+                           int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
+  static int s_sms = -1, s_per_sm = 1;
+  if (s_sms < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s_per_sm, jacobi_onesided_kernel<NPL>, 256, 0);
+    if (s_per_sm < 1) s_per_sm = 1;
+  }
+  int mp = n + (n & 1);
+  int tasks = nmat * (mp / 2);
+  // one block per SM (up to the task count): tasks are dealt round-robin over blocks
+  int blocks = tasks < s_sms ? tasks : s_sms;
+  if (blocks > s_sms * s_per_sm) blocks = s_sms * s_per_sm;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&W, &V, &A, &n, &nmat, &max_sweeps, &counters, &sweeps_out, &st};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_onesided_kernel<NPL>, dim3(blocks),
+                                              dim3(256), args, 0, s);
+  ++g_launches;
+  return e == cudaSuccess ? 0 : -1;
+}
+
+int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
+                  int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
+  int npl = (n + 31) / 32;
+  if (npl <= 1) return launch_jacobi_t<1>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  if (npl <= 2) return launch_jacobi_t<2>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  if (npl <= 4) return launch_jacobi_t<4>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  if (npl <= 8) return launch_jacobi_t<8>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  if (npl <= 16) return launch_jacobi_t<16>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  if (npl <= 32) return launch_jacobi_t<32>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Choice, truncation and sign gauge for one transverse leg.
+// Matrices 2*leg (A^(j)) and 2*leg+1 (A'^(j)) of the Jacobi batch are used.
+// Orders the eigenpairs by lambda descending; values within 1e-12 lambda_1 of
+// their predecessor form a tie group ordered by pivot index (the lowest row
+// whose magnitude is within 1e-6 of the column maximum).  epsilon = sum of the
+// eigenvalues after the first nnew; U^(j) is taken if epsilon < epsilon' -
+// 1e-10 max(lambda_1, lambda'_1), else U'^(j); each kept column is flipped so
+// that its pivot entry is positive.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ W,
+                                                     const double* __restrict__ V, int n,
+                                                     int leg_index, int nnew, double* lam_sorted,
+                                                     double* U64, float* U32, LegResult* res) {
+  extern __shared__ double sm[];
+  double* lam = sm;                         // [2][n]
+  int* piv = (int*)(lam + 2 * n);           // [2][n]
+  int* sgn = piv + 2 * n;                   // [2][n]
+  int* order = sgn + 2 * n;                 // [2][n]
+  __shared__ double s_eps[2];
+  __shared__ int s_choice;
+  const long long nn = (long long)n * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int side = 0; side < 2; ++side) {
+    const double* Wm = W + (long long)(2 * leg_index + side) * nn;
+    const double* Vm = V + (long long)(2 * leg_index + side) * nn;
+    for (int i = warp; i < n; i += nwarps) {
+      double s2 = 0.0, vmax = 0.0;
+      for (int k = lane; k < n; k += 32) {
+        double w = Wm[(long long)i * n + k];
+        s2 = fma(w, w, s2);
+        vmax = fmax(vmax, fabs(Vm[(long long)i * n + k]));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      }
+      int first = n;
+      for (int k0 = 0; k0 < n && first == n; k0 += 32) {
+        int k = k0 + lane;
+        bool hit = k < n && fabs(Vm[(long long)i * n + k]) >= (1.0 - 1e-6) * vmax;
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) first = k0 + __ffs(m) - 1;
+      }
+      if (lane == 0) {
+        lam[side * n + i] = sqrt(s2);
+        piv[side * n + i] = first;
+        sgn[side * n + i] = Vm[(long long)i * n + first] < 0.0 ? -1 : 1;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    int side = e / n, i = e % n;
+    const double* l = lam + side * n;
+    double li = l[i];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += (l[k] > li) || (l[k] == li && k < i);
+    order[side * n + rank] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    int side = threadIdx.x;
+    const double* l = lam + side * n;
+    int* ord = order + side * n;
+    const int* pv = piv + side * n;
+    double tol = 1e-12 * l[ord[0]];
+    int g0 = 0;
+    for (int r = 1; r <= n; ++r) {
+      bool brk = (r == n) || (l[ord[r - 1]] - l[ord[r]] > tol);
+      if (brk) {
+        // insertion sort of ord[g0 .. r-1] by pivot index
+        for (int a = g0 + 1; a < r; ++a) {
+          int key = ord[a];
+          int b = a - 1;
+          while (b >= g0 && pv[ord[b]] > pv[key]) {
+            ord[b + 1] = ord[b];
+            --b;
+          }
+          ord[b + 1] = key;
+        }
+        g0 = r;
+      }
+    }
+    double eps = 0.0;
+    for (int r = nnew; r < n; ++r) eps += l[ord[r]];
+    s_eps[side] = eps;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l1a = lam[order[0]], l1b = lam[n + order[n]];
+    double tol = 1e-10 * fmax(l1a, l1b);
+    int prime = !(s_eps[0] < s_eps[1] - tol) ? 1 : 0;
+    s_choice = prime;
+    const double* lc = lam + prime * n;
+    const int* oc = order + prime * n;
+    res->eps[0] = s_eps[0];
+    res->eps[1] = s_eps[1];
+    res->lam1[0] = l1a;
+    res->lam1[1] = l1b;
+    res->chose_prime = prime;
+    res->gap = (nnew < n && lc[oc[0]] > 0.0) ? (lc[oc[nnew - 1]] - lc[oc[nnew]]) / lc[oc[0]] : 1e300;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    int side = e / n, r = e % n;
+    lam_sorted[e] = lam[side * n + order[side * n + r]];
+  }
+  const int side = s_choice;
+  const double* Vm = V + (long long)(2 * leg_index + side) * nn;
+  for (int e = threadIdx.x; e < n * nnew; e += blockDim.x) {
+    int row = e / nnew, col = e % nnew;
+    int src = order[side * n + col];
+    double v = Vm[(long long)src * n + row] * (double)sgn[side * n + src];
+    U64[e] = v;
+    U32[e] = (float)v;
+  }
+}
+
+void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
+                   double* lam_sorted, double* U64, float* U32, LegResult* res,
+                   int* scratch_order, cudaStream_t s) {
+  (void)scratch_order;
+  size_t smem = (size_t)2 * n * sizeof(double) + (size_t)6 * n * sizeof(int);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  select_kernel<<<1, 512, smem, s>>>(W, V, n, leg_index, nnew, lam_sorted, U64, U32, res);
+  ++g_launches;
+}
+
+}  // namespace hotrg

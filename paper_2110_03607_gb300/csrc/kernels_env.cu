@@ -1,0 +1,141 @@
+// FP64 environment build (Sec. 3.2, Eqs. Aux_Tensor_hat_S / Aux_Tensor_check_S;
+// Sec. 4.2.4) and the plain FP64 contraction GEMM.
+//
+// Each S tensor is a Gram matrix: with X = T permuted to [(n_j, rho) | rest],
+// S_{(f rho),(g eta)} = sum_rest X[(f, rho), rest] X[(g, eta), rest].  The
+// GEMM below computes C = A . B^T for K-contiguous A and B (an "NT" GEMM) in
+// FP64 DFMA tiles, with split-K partial outputs so that every SM has work.
+#include "hotrg_internal.cuh"
+
+namespace hotrg {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16;
+}
+
+// C[z][i][j] = sum_{k in split z} A[i*lda + k] * B[j*ldb + k]
+__global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
+    const double* __restrict__ A, long long lda, const double* __restrict__ B, long long ldb,
+    double* __restrict__ C, long long ldc, long long split_stride, int M, int N, long long K,
+    long long kchunk, int upper_only) {
+  if (upper_only && blockIdx.y > blockIdx.x) return;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const long long k_lo = (long long)blockIdx.z * kchunk;
+  long long k_hi = k_lo + kchunk;
+  if (k_hi > K) k_hi = K;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  // loader mapping: 64 rows x 16 k; thread -> (row = tid / 4, k = (tid % 4) * 4 .. +3)
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (long long k0 = k_lo; k0 < k_hi; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      long long k = k0 + lk + u;
+      int ra = m0 + lr, rb = n0 + lr;
+      As[lk + u][lr] = (ra < M && k < k_hi) ? A[(long long)ra * lda + k] : 0.0;
+      Bs[lk + u][lr] = (rb < N && k < k_hi) ? B[(long long)rb * ldb + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* Cz = C + (long long)blockIdx.z * split_stride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = m0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = n0 + tx + 16 * j;
+      if (c < N) Cz[(long long)r * ldc + c] = acc[i][j];
+    }
+  }
+}
+
+void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
+                        long long ldc, long long split_stride, int M, int N, long long K,
+                        int nsplit, int upper_only, cudaStream_t s) {
+  if (nsplit < 1) nsplit = 1;
+  long long kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  nsplit = (int)((K + kchunk - 1) / kchunk);
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
+  gemm_nt_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, split_stride, M, N, K, kchunk,
+                                           upper_only);
+  ++g_launches;
+}
+
+// G[i][j] = sum_z parts[z][min(i,j)][max(i,j)]  (exactly symmetric)
+__global__ void reduce_sym_kernel(const double* __restrict__ parts, int nsplit, int m,
+                                  double* __restrict__ G) {
+  long long total = (long long)m * m;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), j = (int)(e % m);
+    int lo = i < j ? i : j, hi = i < j ? j : i;
+    double acc = 0.0;
+    for (int z = 0; z < nsplit; ++z) acc += parts[(long long)z * total + (long long)lo * m + hi];
+    G[e] = acc;
+  }
+}
+
+void launch_reduce_sym(const double* parts, int nsplit, int m, double* G, cudaStream_t s) {
+  long long total = (long long)m * m;
+  int blocks = (int)((total + 255) / 256);
+  reduce_sym_kernel<<<blocks, 256, 0, s>>>(parts, nsplit, m, G);
+  ++g_launches;
+}
+
+// A_{(f^ + f~ chi),(g^ + g~ chi)} = sum_{rho, eta} S^_{(f^ rho),(g^ eta)} S~_{(f~ rho),(g~ eta)}
+// (Sec. 3.2, last step; S rows are (n_j, current) with n_j the slow index).
+// Computed for the upper triangle and mirrored, so A is exactly symmetric.
+__global__ void assemble_a_kernel(const double* __restrict__ sh, const double* __restrict__ sc,
+                                  int chi, int chc, double* __restrict__ A) {
+  int n = chi * chi;
+  int m = chi * chc;
+  long long total = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    if (i > j) continue;
+    int fh = i % chi, fc = i / chi, gh = j % chi, gc = j / chi;
+    const double* shr = sh + (long long)(fh * chc) * m + gh * chc;
+    const double* scr = sc + (long long)(fc * chc) * m + gc * chc;
+    double acc = 0.0;
+    for (int rho = 0; rho < chc; ++rho)
+      for (int eta = 0; eta < chc; ++eta)
+        acc = fma(shr[(long long)rho * m + eta], scr[(long long)rho * m + eta], acc);
+    A[(long long)i * n + j] = acc;
+    A[(long long)j * n + i] = acc;
+  }
+}
+
+void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int chi_c, double* A,
+                       cudaStream_t s) {
+  long long total = (long long)chi_j * chi_j * chi_j * chi_j;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  assemble_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(s_hat, s_chk, chi_j, chi_c, A);
+  ++g_launches;
+}
+
+}  // namespace hotrg

@@ -1,0 +1,210 @@
+"""GPU HOTRG steps through the C ABI against the FP64 oracle and exact results."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hotrg_oracle as o
+from tests import exact_ising as ex
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    import paper_2110_03607_gb300 as p
+
+    assert torch.cuda.is_available()
+    p.load()
+    return p
+
+
+def _gpu_run(pkg, d, beta, h, chi, axes, prec, fp64_below=0.0):
+    # fp64_below = 0 forces the split-BF16 contraction even on tiny steps
+    g = pkg.Hotrg(d, beta, h, precision=prec, fp64_below=fp64_below)
+    out = []
+    try:
+        for a in axes:
+            g.step(a, chi)
+            lnz, _ = g.free_energy()
+            tr, x, _ = pkg.hotrg_observables(g.ctx)
+            out.append((lnz, tr, x))
+    finally:
+        g.close()
+    return out
+
+
+@pytest.mark.parametrize("d,nsteps,chi", [(2, 4, 16), (3, 3, 16)])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_untruncated_gpu_run_equals_brute_force(pkg, d, nsteps, chi, prec):
+    beta, h = 0.3, 0.1
+    axes = o.cyclic_axes(d, nsteps, first=d - 1)
+    res = _gpu_run(pkg, d, beta, h, chi, axes, prec)
+    tol = 1e-12 if prec == 0 else 5e-7
+    for i, (lnz, _, _) in enumerate(res):
+        exact = ex.brute_force_ln_z(ex.lattice_after(d, axes[: i + 1]), beta, h) / 2 ** (i + 1)
+        assert abs(lnz - exact) / abs(exact) <= tol, (i, lnz, exact)
+
+
+@pytest.mark.parametrize("d,chi,nsteps,beta,h", [
+    (2, 8, 12, 0.4406868, 0.0),
+    (2, 5, 8, 0.3, 0.05),
+    (3, 4, 7, 0.2216544, 0.0),
+    (4, 3, 6, 0.15, 0.0),
+])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (2, 5e-7), (1, 5e-6)])
+def test_gpu_run_matches_oracle(pkg, d, chi, nsteps, beta, h, prec, tol):
+    # split modes forced onto every step (tiny steps weigh most: looser gates)
+    axes = o.cyclic_axes(d, nsteps)
+    res = _gpu_run(pkg, d, beta, h, chi, axes, prec)
+    run = o.HotrgRun(d, beta, h)
+    for i, a in enumerate(axes):
+        rec = run.step(a, chi)
+        lnz, tr, x = res[i]
+        assert abs(lnz - rec.ln_z_per_site) / abs(rec.ln_z_per_site) <= tol, (i, lnz, rec.ln_z_per_site)
+        assert abs(x - rec.gu_wen_x) <= 1e3 * tol * abs(rec.gu_wen_x)
+
+
+def test_single_step_isometry_spectrum_and_tensor_match_oracle(pkg):
+    # input: an oracle tensor after two steps (3D, bonds (4, 4, 2)); step along x
+    run = o.HotrgRun(3, 0.25, 0.02)
+    run.step(2, 16)
+    run.step(0, 16)
+    t_in = run.t.copy()
+    chis = [t_in.shape[2 * k] for k in range(3)]
+    chi = 7
+    ctx = pkg.hotrg_init_tensor(3, chis, t_in, 0.25)
+    try:
+        pkg.hotrg_set_precision(ctx, pkg.PREC_FP64)
+        pkg.hotrg_step(ctx, 1, chi)
+        ref = o.HotrgRun(3, 0.25, 0.0, tensor=t_in)
+        rec = ref.step(1, chi)
+        for leg in rec.legs:
+            for prime in (0, 1):
+                lam = pkg.hotrg_spectrum(ctx, leg.axis, prime)
+                want = leg.lam_prime if prime else leg.lam
+                np.testing.assert_allclose(lam, want, rtol=0, atol=1e-12 * want[0])
+            u, chose_prime = pkg.hotrg_isometry(ctx, leg.axis)
+            assert u.shape == leg.u.shape
+            np.testing.assert_allclose(u.T @ u, np.eye(u.shape[1]), atol=1e-12)
+            if leg.gap_at_cut > 1e-6:
+                np.testing.assert_allclose(u, leg.u, atol=1e-9)
+        t_gpu = pkg.hotrg_tensor(ctx)
+        np.testing.assert_allclose(t_gpu, ref.t, rtol=0, atol=1e-10 * np.abs(ref.t).max())
+        lnz, _ = pkg.hotrg_free_energy(ctx)
+        assert lnz == pytest.approx(rec.ln_z_per_site, rel=1e-13)
+    finally:
+        pkg.hotrg_free(ctx)
+
+
+def test_default_policy_keeps_early_steps_exact(pkg):
+    # BF16 modes contract steps below 2^36 flops in FP64: the untruncated 4x4 lattice
+    # is then reproduced to FP64 accuracy
+    beta, h = 0.3, 0.1
+    axes = o.cyclic_axes(2, 4, first=1)
+    res = _gpu_run(pkg, 2, beta, h, 16, axes, 2, fp64_below=2.0 ** 36)
+    for i, (lnz, _, _) in enumerate(res):
+        exact = ex.brute_force_ln_z(ex.lattice_after(2, axes[: i + 1]), beta, h) / 2 ** (i + 1)
+        assert abs(lnz - exact) / abs(exact) <= 1e-12
+
+
+def test_beta_zero_gives_ln2(pkg):
+    res = _gpu_run(pkg, 3, 0.0, 0.0, 4, o.cyclic_axes(3, 5), 2)
+    for lnz, _, _ in res:
+        assert lnz == pytest.approx(math.log(2.0), rel=1e-12)
+
+
+def test_errors_are_reported(pkg):
+    g = pkg.Hotrg(2, 0.3, 0.0, precision=0)
+    try:
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_step(g.ctx, 5, 4)
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_step(g.ctx, 0, 0)
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_isometry(g.ctx, 0)     # no step yet
+        g.step(0, 4)
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_isometry(g.ctx, 0)     # axis 0 was the step's own axis
+        pkg.hotrg_isometry(g.ctx, 1)
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------------------
+# full size: 3D Ising, chi = 16 (the benchmark workload and launch configuration)
+# ---------------------------------------------------------------------------
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name + ".jsonl")
+    out = {}
+    for line in open(path):
+        r = json.loads(line)
+        if r.get("kind") == "step":
+            out[r["step"]] = r
+    return out
+
+
+def test_ising3d_chi16_free_energy_matches_oracle_reference(pkg):
+    gold = _golden("ising3d_chi16")
+    assert len(gold) >= 5
+    g = pkg.Hotrg(3, 0.2216544, 0.0, precision=pkg.PREC_BF16X6)
+    try:
+        for step in range(1, max(gold) + 1):
+            g.step((2 + step - 1) % 3, 16)
+            lnz, _ = g.free_energy()
+            ref = gold[step]["ln_z_per_site"]
+            assert abs(lnz - ref) / abs(ref) <= 1e-7, (step, lnz, ref)
+            _, x, _ = pkg.hotrg_observables(g.ctx)
+            assert abs(x - gold[step]["gu_wen_x"]) <= 1e-5
+            for leg in gold[step]["legs"]:
+                lam = pkg.hotrg_spectrum(g.ctx, leg["axis"], 0)
+                want = np.array(leg["lam"])
+                np.testing.assert_allclose(lam[: len(want)], want, rtol=0, atol=1e-6 * want[0])
+    finally:
+        g.close()
+
+
+def test_ising3d_chi16_sampled_new_tensor_elements(pkg):
+    # input: the oracle's tensor after steps z, x, y (bonds 16, 16, 16); one
+    # full-size step along z on the GPU (split-BF16 bottleneck, the bench's
+    # configuration); sampled (c', n') slabs of T_new computed by the oracle.
+    run = o.HotrgRun(3, 0.2216544, 0.0)
+    for a in (2, 0, 1):
+        run.step(a, 16)
+    t_in = run.t
+    ctx = pkg.hotrg_init_tensor(3, [16, 16, 16], t_in, 0.2216544)
+    try:
+        pkg.hotrg_set_precision(ctx, pkg.PREC_BF16X6)
+        pkg.hotrg_step(ctx, 2, 16)
+        tr_gpu, _, _ = pkg.hotrg_observables(ctx)
+        t_gpu = pkg.hotrg_tensor(ctx) * tr_gpu          # undo the normalisation
+        tp = o.to_paper_order(t_in, 2)
+        nxt = o.next_axes(3, 2)
+        legs = [o.choose_isometry(tp, j, 16, nxt[j - 1]) for j in (1, 2)]
+        for leg in legs:
+            lam = pkg.hotrg_spectrum(ctx, leg.axis, 1 if leg.chose_prime else 0)
+            want = leg.lam_prime if leg.chose_prime else leg.lam
+            np.testing.assert_allclose(lam, want, rtol=0, atol=1e-12 * want[0])
+            u, _ = pkg.hotrg_isometry(ctx, leg.axis)
+            np.testing.assert_allclose(u.T @ u, np.eye(16), atol=1e-12)
+            assert leg.gap_at_cut > 1e-6
+            np.testing.assert_allclose(u, leg.u, atol=1e-8)
+        tgpu_p = o.to_paper_order(t_gpu, 2)      # [n2, n1, n2', n1', c, c']
+        that = o.hat_matrix(tp)
+        rng = np.random.default_rng(5)
+        for _ in range(6):
+            c0p = int(rng.integers(16))
+            npr = (int(rng.integers(16)), int(rng.integers(16)))
+            slab = o.new_tensor_slab(tp, [leg.u for leg in legs], c0p, npr, that)   # [c, n2, n1]
+            got = tgpu_p[:, :, npr[1], npr[0], :, c0p]                         # [n2, n1, c]
+            got = np.moveaxis(got, -1, 0)
+            scale = np.abs(slab).max()
+            np.testing.assert_allclose(got, slab, rtol=0, atol=2e-6 * scale)
+    finally:
+        pkg.hotrg_free(ctx)
