@@ -70,23 +70,42 @@ long long stride_of(const View& v, int name, bool* found = nullptr) {
   return 0;
 }
 
-ChainDesc make_stage(const View& in, const View& out, int a_name, int b_name, int n_name, int chi,
-                     int nn) {
-  ChainDesc d;
+// Returns false if the free dimensions do not fit the descriptor.
+bool make_stage(ChainDesc& d, const View& in, const View& out, int a_name, int b_name, int n_name,
+                int chi, int nn) {
   memset(&d, 0, sizeof(d));
-  View fr;
+  struct Fd {
+    int name;
+    long long size, ist, ost;
+  };
+  std::vector<Fd> fr;
   for (auto& o : out)
-    if (o.name != n_name) fr.push_back(o);
-  std::stable_sort(fr.begin(), fr.end(), [](const Ix& a, const Ix& b) { return a.stride < b.stride; });
-  d.ndim = (int)fr.size();
+    if (o.name != n_name && o.size > 1) fr.push_back({o.name, o.size, stride_of(in, o.name), o.stride});
+  for (auto& o : out)
+    if (o.name == a_name && o.size == 1) fr.push_back({o.name, 1, 0, o.stride});
+  std::stable_sort(fr.begin(), fr.end(), [](const Fd& a, const Fd& b) { return a.ost < b.ost; });
+  // merge neighbours that are contiguous in both input and output (never the hat index)
+  std::vector<Fd> mg;
+  for (auto& f : fr) {
+    if (!mg.empty()) {
+      Fd& b = mg.back();
+      if (b.name != a_name && f.name != a_name && f.ost == b.ost * b.size && f.ist == b.ist * b.size) {
+        b.size *= f.size;
+        continue;
+      }
+    }
+    mg.push_back(f);
+  }
+  if ((int)mg.size() > kMaxDims) return false;
+  d.ndim = (int)mg.size();
   d.a_dim = -1;
   d.total = 1;
   for (int k = 0; k < d.ndim; ++k) {
-    d.size[k] = fr[k].size;
-    d.out_stride[k] = fr[k].stride;
-    d.in_stride[k] = stride_of(in, fr[k].name);
-    if (fr[k].name == a_name) d.a_dim = k;
-    d.total *= fr[k].size;
+    d.size[k] = mg[k].size;
+    d.out_stride[k] = mg[k].ost;
+    d.in_stride[k] = mg[k].ist;
+    if (mg[k].name == a_name) d.a_dim = k;
+    d.total *= mg[k].size;
   }
   d.ka_stride = d.a_dim >= 0 ? 0 : stride_of(in, a_name);
   d.kb_stride = stride_of(in, b_name);
@@ -94,7 +113,7 @@ ChainDesc make_stage(const View& in, const View& out, int a_name, int b_name, in
   d.chi = chi;
   d.nn = nn;
   d.npieces = 1;
-  return d;
+  return true;
 }
 
 }  // namespace
@@ -763,7 +782,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         out.push_back({I_RHO, chi_c, P});
         for (int k = 1; k < d; ++k) out.push_back({I_NHP + k, chij[k], prod_after(chij, k)});
       }
-      ChainDesc cd = make_stage(in, out, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nnew[j]);
+      ChainDesc cd;
+      if (!make_stage(cd, in, out, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nnew[j])) {
+        c->poisoned = HOTRG_EINVAL;
+        return HOTRG_EINVAL;
+      }
       void* dst = last ? c->Bp.p : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
         launch_chain_f64(cd, (const double*)src, (const double*)c->U64.p + u_off[j], (double*)dst, s);
@@ -819,7 +842,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         for (int k = 1; k < d; ++k) out.push_back({I_N + k, nnew[k], prod_after(nnew, k) * Rn});
         for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nnew[k], prod_after(nnew, k)});
       }
-      ChainDesc cd = make_stage(cin, out, I_NH + j, I_NC + j, I_N + j, chij[j], nnew[j]);
+      ChainDesc cd;
+      if (!make_stage(cd, cin, out, I_NH + j, I_NC + j, I_N + j, chij[j], nnew[j])) {
+        c->poisoned = HOTRG_EINVAL;
+        return HOTRG_EINVAL;
+      }
       void* dst = last ? (void*)(Tn + (long long)sl * Pn) : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
         launch_chain_f64(cd, (const double*)csrc, (const double*)c->U64.p + u_off[j], (double*)dst, s);

@@ -8,7 +8,7 @@
 namespace hotrg {
 
 constexpr int kMaxD = 4;
-constexpr int kMaxDims = 8;      // tensor ranks handled by the index kernels
+constexpr int kMaxDims = 10;     // tensor ranks handled by the index kernels
 constexpr int kMaxBond = 64;
 
 // Device-side state of a run; lives in device memory, read back on demand.

@@ -12,6 +12,9 @@
 
 namespace hotrg {
 
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(double x) { return __double2bfloat16(x); }
+
 template <typename TIn, typename TAcc, int NN, int OUT>
 __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
                                                     const TAcc* __restrict__ U, void* out) {
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
         TAcc x = acc[n];
         long long off = out_off + n * d.n_out_stride;
         for (int p = 0; p < d.npieces; ++p) {
-          __nv_bfloat16 bv = __double2bfloat16((double)x);
+          __nv_bfloat16 bv = to_bf16(x);
           o[off + p * d.piece_stride] = bv;
           x -= (TAcc)__bfloat162float(bv);
         }
