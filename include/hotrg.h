@@ -167,6 +167,30 @@ int hotrg_tensor(hotrg_ctx* ctx, double* T, int64_t cap, int dims[8]);
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* B, double* C);
 
+/* hotrg_gemm_nt without any device allocation (the paper has no counterpart;
+ * this serves callers that cannot allocate).  Some callers may not call
+ * cudaMalloc or cudaFree: code running inside a framework that owns all
+ * device memory through its own pool (a raw allocation bypasses the pool and
+ * can fail once the pool has reserved the memory), and latency-critical
+ * loops where cudaMalloc/cudaFree would synchronise the device.  This entry
+ * point computes C[M][N] = sum_k A[M][K] B[N][K] like hotrg_gemm_nt, but A, B
+ * and C must be DEVICE pointers (FP64, row-major) owned by the caller, and all
+ * scratch (BF16 pieces, FP32 product, error word) lives in one fixed
+ * file-scope device array of HOTRG_NOALLOC_SCRATCH_BYTES (64 MiB) that every
+ * GPU loading the library keeps until the process exits.  Sizes whose scratch
+ * exceeds it -- 2*np*(M+N)*ceil64(K) + 4*M*N bytes, np = 2 (BF16X3) or 3 --
+ * are rejected with HOTRG_EINVAL.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+ * returns after synchronising it.  Every call shares the one array: calls
+ * that overlap on the GPU (other streams, other threads) race and must not
+ * be issued.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: EINVAL, ECUDA, ETIMEOUT. */
+#define HOTRG_NOALLOC_SCRATCH_BYTES (64u << 20)
+int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double* A, const double* B,
+                          double* C, void* stream);
+
 /* Bytes of device memory the context holds now. */
 int hotrg_device_bytes(hotrg_ctx* ctx, size_t* bytes);
 
