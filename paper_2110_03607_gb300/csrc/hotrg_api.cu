@@ -113,6 +113,16 @@ bool make_stage(ChainDesc& d, const View& in, const View& out, int a_name, int b
   d.chi = chi;
   d.nn = nn;
   d.npieces = 1;
+  if (d.total >= (1LL << 32)) return false;
+  for (int k = 0; k < d.ndim; ++k) {
+    // Hacker's Delight unsigned division by an invariant: l = ceil(log2 s),
+    // m = floor(2^32 (2^l - s) / s) + 1, x / s = (umulhi(x, m) + x) >> l
+    unsigned long long sz = (unsigned long long)d.size[k];
+    int l = 0;
+    while ((1ULL << l) < sz) ++l;
+    d.shift[k] = l;
+    d.magic[k] = (unsigned)((((1ULL << l) - sz) << 32) / sz + 1);
+  }
   return true;
 }
 
@@ -151,6 +161,7 @@ struct hotrg_ctx {
   // buffers
   Buf T, T2, Xp, parts, S, Amat, W, V, lam, U64, U32, legres, Y, state, counters, sweeps;
   Buf Ap, Bp, Cb, chA, chB;
+  Buf J32, Gns, Vtmp;   // eigen-solver warm start
 };
 
 namespace {
@@ -227,6 +238,17 @@ struct Phase {
       return _r;                       \
     }                                  \
   } while (0)
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n < 1) n = 148;
+  }
+  return n;
+}
 
 int cuda_status(hotrg_ctx* c) {
   cudaError_t e = cudaGetLastError();
@@ -481,7 +503,8 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   int n = 0;
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
-              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB};
+              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
+              &c->J32,  &c->Gns, &c->Vtmp};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
@@ -605,12 +628,15 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     mmax = std::max<long long>(mmax, (long long)chij[j] * chi_c);
     nmax = std::max<long long>(nmax, (long long)chij[j] * chij[j]);
   }
-  const int nsplit_max = 64;
+  const int nsplit_max = 128;
   CHECK_ALLOC(dev_alloc(c, c->parts, sizeof(double) * nsplit_max * mmax * mmax));
   CHECK_ALLOC(dev_alloc(c, c->S, sizeof(double) * 4 * nlegs * mmax * mmax));
   CHECK_ALLOC(dev_alloc(c, c->Amat, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->W, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->V, sizeof(double) * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->J32, sizeof(float) * 2 * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->Gns, sizeof(double) * total_mat_elems));
+  CHECK_ALLOC(dev_alloc(c, c->Vtmp, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * 3 * 2 * kMaxD));
   CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 2 * kMaxD));
 
@@ -635,9 +661,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         ist[nd++] = q < d ? rs[q] : cs[q - d];
       }
       launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
+      // fill every SM with the same number of CTAs: tiles x splits <= 4 per SM
       int tiles = (int)((m + 63) / 64);
       int upper_tiles = tiles * (tiles + 1) / 2;
-      int nsplit = std::max(1, std::min<int>(nsplit_max, (2 * 152 + upper_tiles - 1) / upper_tiles));
+      int nsplit = std::max(1, std::min<int>(nsplit_max, (4 * num_sms() ) / upper_tiles));
       nsplit = (int)std::min<long long>(nsplit, std::max<long long>(1, K / 64));
       launch_gemm_nt_f64((const double*)c->Xp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p,
                          m, m * m, (int)m, (int)m, K, nsplit, 1, s);
@@ -664,8 +691,32 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         cnt += 2;
         if (base < 0 || mat_elem_off[2 * j] < base) base = mat_elem_off[2 * j];
       }
-    if (launch_jacobi((double*)c->W.p + base, (double*)c->V.p + base, (const double*)c->Amat.p + base,
-                      grp_n[g], cnt, 60, (int*)c->counters.p, (int*)c->sweeps.p,
+    const int n = grp_n[g];
+    const long long nn = (long long)n * n;
+    double* Wg = (double*)c->W.p + base;
+    double* Vg = (double*)c->V.p + base;
+    const double* Ag = (const double*)c->Amat.p + base;
+    const double* Ainit = Ag;
+    if (n >= 32) {
+      // FP32 warm start, FP64 re-orthonormalisation of its vectors (two Newton-Schulz
+      // steps Q <- Q (3I - Q^T Q) / 2), W = A Q; the FP64 sweeps then start from (W, Q)
+      float* W32 = (float*)c->J32.p;
+      float* V32 = W32 + cnt * nn;
+      double* G = (double*)c->Gns.p;
+      double* Vt = (double*)c->Vtmp.p;
+      if (launch_jacobi32(Ag, W32, V32, n, cnt, 40, s) == 0) {
+        launch_widen_f32(V32, Vg, cnt * nn, s);
+        for (int it = 0; it < 2; ++it) {
+          launch_gemm_nt_f64_batched(Vg, n, Vg, n, G, n, n, n, n, cnt, nn, nn, nn, s);
+          launch_ns_coeff(G, n, cnt, s);
+          launch_gemm_nn_f64(G, n, Vg, n, Vt, n, n, n, n, cnt, nn, nn, nn, s);
+          cudaMemcpyAsync(Vg, Vt, sizeof(double) * cnt * nn, cudaMemcpyDeviceToDevice, s);
+        }
+        launch_gemm_nt_f64_batched(Vg, n, Ag, n, Wg, n, n, n, n, cnt, nn, nn, nn, s);
+        Ainit = nullptr;
+      }
+    }
+    if (launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p, (int*)c->sweeps.p,
                       (DevState*)c->state.p, s) != 0)
       return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
   }
@@ -1095,7 +1146,8 @@ void hotrg_free(hotrg_ctx* c) {
   cudaGetLastError();
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
-              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB};
+              &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
+              &c->J32,  &c->Gns, &c->Vtmp};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
   delete c;

@@ -47,7 +47,9 @@ struct ChainDesc {
   long long out_stride[kMaxDims];
   long long ka_stride, kb_stride;
   long long n_out_stride;
-  long long total;     // product of size[]
+  long long total;     // product of size[] (< 2^32)
+  unsigned magic[kMaxDims];   // q = (umulhi(x, magic) + x) >> shift == x / size, 32-bit x
+  int shift[kMaxDims];
   long long piece_stride;  // split outputs: distance between BF16 pieces
   int npieces;
 };
@@ -74,6 +76,16 @@ void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int 
 // ---- kernels_eig.cu
 int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
                   int* counters, int* sweeps_out, DevState* st, cudaStream_t s);
+int launch_jacobi32(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
+                    cudaStream_t s);
+void launch_widen_f32(const float* in, double* out, long long n, cudaStream_t s);
+void launch_ns_coeff(double* G, int n, int nmat, cudaStream_t s);
+void launch_gemm_nn_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
+                        long long ldc, int M, int N, int K, int batch, long long bsa,
+                        long long bsb, long long bsc, cudaStream_t s);
+void launch_gemm_nt_f64_batched(const double* A, long long lda, const double* B, long long ldb,
+                                double* C, long long ldc, int M, int N, int K, int batch,
+                                long long bsa, long long bsb, long long bsc, cudaStream_t s);
 void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
                    double* lam_sorted, double* U64, float* U32, LegResult* res,
                    int* scratch_order, cudaStream_t s);

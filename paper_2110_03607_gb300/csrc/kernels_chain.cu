@@ -29,17 +29,18 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.total; t += stride) {
-    long long rem = t, in_off = 0, out_off = 0;
+    unsigned rem = (unsigned)t;
+    long long in_off = 0, out_off = 0;
     int a_val = 0;
 #pragma unroll
     for (int k = 0; k < kMaxDims; ++k) {
       if (k >= d.ndim) break;
-      long long sz = d.size[k];
-      long long q = rem / sz;
-      long long idx = rem - q * sz;
+      // rem / size[k] by multiply-shift (sizes and magics prepared on the host)
+      unsigned q = (unsigned)(((unsigned long long)__umulhi(rem, d.magic[k]) + rem) >> d.shift[k]);
+      unsigned idx = rem - q * (unsigned)d.size[k];
       rem = q;
-      in_off += idx * d.in_stride[k];
-      out_off += idx * d.out_stride[k];
+      in_off += (long long)idx * d.in_stride[k];
+      out_off += (long long)idx * d.out_stride[k];
       if (k == d.a_dim) a_val = (int)idx;
     }
     TAcc acc[NN];

@@ -37,11 +37,14 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
   const long long nn = (long long)n * n;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gthreads = (long long)gridDim.x * blockDim.x;
-  for (long long e = gtid; e < (long long)nmat * nn; e += gthreads) {
-    long long r = e % nn;
-    int i = (int)(r / n), j = (int)(r % n);
-    __stcg(W + e, A[e]);                // A symmetric: row i = column i
-    __stcg(V + e, i == j ? 1.0 : 0.0);
+  // A == nullptr: W and V already hold a starting point (W = A V, V orthogonal)
+  if (A) {
+    for (long long e = gtid; e < (long long)nmat * nn; e += gthreads) {
+      long long r = e % nn;
+      int i = (int)(r / n), j = (int)(r % n);
+      __stcg(W + e, A[e]);                // A symmetric: row i = column i
+      __stcg(V + e, i == j ? 1.0 : 0.0);
+    }
   }
   if (gtid < 3 * nmat) counters[gtid] = 0;
   grid.sync();
@@ -160,6 +163,130 @@ int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int ma
   if (npl <= 16) return launch_jacobi_t<16>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
   if (npl <= 32) return launch_jacobi_t<32>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
   return -1;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 warm start: the same one-sided Jacobi in single precision, one CTA per
+// matrix (rounds separated by __syncthreads, no grid barrier).  Its vectors
+// only seed the FP64 sweeps, which restore full accuracy; it stops at FP32
+// tolerance or after max_sweeps without raising an error.
+// ---------------------------------------------------------------------------
+template <int NPL>
+__global__ void __launch_bounds__(1024) jacobi32_kernel(const double* __restrict__ A, float* W,
+                                                        float* V, int n, int max_sweeps) {
+  __shared__ int s_rot;
+  const long long nn = (long long)n * n;
+  float* Wm = W + blockIdx.x * nn;
+  float* Vm = V + blockIdx.x * nn;
+  const double* Am = A + blockIdx.x * nn;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    Wm[e] = (float)Am[e];
+    Vm[e] = (e / n == e % n) ? 1.0f : 0.0f;
+  }
+  const int mp = n + (n & 1), npairs = mp / 2, rounds = mp - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float tol = 4.0f * (float)n * 1.1920929e-7f;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < rounds; ++r) {
+      for (int k = warp; k < npairs; k += nw) {
+        int p = rr_slot(k, r, mp), q = rr_slot(mp - 1 - k, r, mp);
+        if (p >= n || q >= n) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        float* wp = Wm + (long long)p * n;
+        float* wq = Wm + (long long)q * n;
+        float xs[NPL], ys[NPL];
+        float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          float x = i < n ? wp[i] : 0.f, y = i < n ? wq[i] : 0.f;
+          xs[u] = x;
+          ys[u] = y;
+          a = fmaf(x, x, a);
+          b = fmaf(y, y, b);
+          g = fmaf(x, y, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (g == 0.f || !(fabsf(g) > tol * sqrtf(a * b))) continue;
+        float zeta = (b - a) / (2.f * g);
+        float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          if (i < n) {
+            wp[i] = c * xs[u] - sn * ys[u];
+            wq[i] = sn * xs[u] + c * ys[u];
+          }
+        }
+        float* vp = Vm + (long long)p * n;
+        float* vq = Vm + (long long)q * n;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          if (i < n) {
+            float x = vp[i], y = vq[i];
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+}
+
+// Q = V32 in FP64, and 0.5 (3 I - G) for the Newton-Schulz step Q <- Q (3I - Q^T Q) / 2
+__global__ void widen_f32_kernel(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (double)in[e];
+}
+
+__global__ void ns_coeff_kernel(double* G, int n, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e % ((long long)n * n);
+    int i = (int)(r / n), j = (int)(r % n);
+    G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+  }
+}
+
+int launch_jacobi32(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
+                    cudaStream_t s) {
+  int npl = (n + 31) / 32;
+  if (npl <= 2) jacobi32_kernel<2><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
+  else if (npl <= 4) jacobi32_kernel<4><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
+  else if (npl <= 8) jacobi32_kernel<8><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
+  else if (npl <= 16) jacobi32_kernel<16><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
+  else if (npl <= 32) jacobi32_kernel<32><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
+  else return -1;
+  ++g_launches;
+  return 0;
+}
+
+void launch_widen_f32(const float* in, double* out, long long n, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  widen_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
+  ++g_launches;
+}
+
+void launch_ns_coeff(double* G, int n, int nmat, cudaStream_t s) {
+  long long total = (long long)nmat * n * n;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  ns_coeff_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, n, total);
+  ++g_launches;
 }
 
 // ---------------------------------------------------------------------------

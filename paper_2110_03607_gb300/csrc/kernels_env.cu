@@ -18,12 +18,23 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
     const double* __restrict__ A, long long lda, const double* __restrict__ B, long long ldb,
     double* __restrict__ C, long long ldc, long long split_stride, int M, int N, long long K,
     long long kchunk, int upper_only) {
-  if (upper_only && blockIdx.y > blockIdx.x) return;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (upper_only) {
+    // blockIdx.x enumerates the tile pairs (ti <= tj) of the upper triangle, row by row
+    const int nt = (M + BM - 1) / BM;
+    int t = blockIdx.x, ti = 0;
+    while (t >= nt - ti) {
+      t -= nt - ti;
+      ++ti;
+    }
+    by = ti;
+    bx = ti + t;
+  }
+  const int n0 = bx * BN, m0 = by * BM;
   const long long k_lo = (long long)blockIdx.z * kchunk;
   long long k_hi = k_lo + kchunk;
   if (k_hi > K) k_hi = K;
@@ -32,17 +43,28 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  // loader mapping: 64 rows x 16 k; thread -> (row = tid / 4, k = (tid % 4) * 4 .. +3)
+  // loader mapping: 64 rows x 16 k; thread -> (row = tid / 4, k = (tid % 4) * 4 .. +3).
+  // The next slab is fetched into registers while the current one is multiplied.
   const int lr = tid >> 2, lk = (tid & 3) * 4;
-  for (long long k0 = k_lo; k0 < k_hi; k0 += BK) {
+  const int ra = m0 + lr, rb = n0 + lr;
+  double pa[4], pb[4];
+  auto fetch = [&](long long k0) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       long long k = k0 + lk + u;
-      int ra = m0 + lr, rb = n0 + lr;
-      As[lk + u][lr] = (ra < M && k < k_hi) ? A[(long long)ra * lda + k] : 0.0;
-      Bs[lk + u][lr] = (rb < N && k < k_hi) ? B[(long long)rb * ldb + k] : 0.0;
+      pa[u] = (ra < M && k < k_hi) ? A[(long long)ra * lda + k] : 0.0;
+      pb[u] = (rb < N && k < k_hi) ? B[(long long)rb * ldb + k] : 0.0;
+    }
+  };
+  if (k_lo < k_hi) fetch(k_lo);
+  for (long long k0 = k_lo; k0 < k_hi; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      As[lk + u][lr] = pa[u];
+      Bs[lk + u][lr] = pb[u];
     }
     __syncthreads();
+    if (k0 + BK < k_hi) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       double a[4], b[4];
@@ -78,9 +100,91 @@ void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long lo
   kchunk = (kchunk + BK - 1) / BK * BK;
   nsplit = (int)((K + kchunk - 1) / kchunk);
   if (nsplit < 1) nsplit = 1;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
+  const int nt = (M + BM - 1) / BM;
+  dim3 grid = upper_only ? dim3(nt * (nt + 1) / 2, 1, nsplit)
+                         : dim3((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
   gemm_nt_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, split_stride, M, N, K, kchunk,
                                            upper_only);
+  ++g_launches;
+}
+
+// Batched small FP64 products for the Newton-Schulz re-orthonormalisation in the
+// eigen-solver: C_b = A_b . op(B_b), op(B) = B^T (B_N = false: B rows are K-contiguous)
+// or B (B_N = true: B[k][j], j contiguous).  64 x 64 tiles, 4 x 4 per thread.
+template <bool B_N>
+__global__ void __launch_bounds__(256) gemm_small_f64_kernel(
+    const double* __restrict__ A, long long lda, const double* __restrict__ B, long long ldb,
+    double* __restrict__ C, long long ldc, int M, int N, int K, long long bsa, long long bsb,
+    long long bsc) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  A += blockIdx.z * bsa;
+  B += blockIdx.z * bsb;
+  C += blockIdx.z * bsc;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int k = k0 + lk + u;
+      int ra = m0 + lr;
+      As[lk + u][lr] = (ra < M && k < K) ? A[(long long)ra * lda + k] : 0.0;
+      if (!B_N) {
+        int rb = n0 + lr;
+        Bs[lk + u][lr] = (rb < N && k < K) ? B[(long long)rb * ldb + k] : 0.0;
+      } else {
+        int kk = tid >> 4, col = (tid & 15) * 4 + u;
+        int kb = k0 + kk;
+        Bs[kk][col] = (kb < K && n0 + col < N) ? B[(long long)kb * ldb + n0 + col] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = m0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = n0 + tx + 16 * j;
+      if (c < N) C[(long long)r * ldc + c] = acc[i][j];
+    }
+  }
+}
+
+void launch_gemm_nn_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
+                        long long ldc, int M, int N, int K, int batch, long long bsa, long long bsb,
+                        long long bsc, cudaStream_t s) {
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  gemm_small_f64_kernel<true><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, bsa, bsb, bsc);
+  ++g_launches;
+}
+
+void launch_gemm_nt_f64_batched(const double* A, long long lda, const double* B, long long ldb,
+                                double* C, long long ldc, int M, int N, int K, int batch,
+                                long long bsa, long long bsb, long long bsc, cudaStream_t s) {
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  gemm_small_f64_kernel<false><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, bsa, bsb, bsc);
   ++g_launches;
 }
 
