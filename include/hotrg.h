@@ -110,7 +110,9 @@ int hotrg_set_fp64_threshold(hotrg_ctx* ctx, double flops);
  * milliseconds of the last step per phase: [0] leg permutation, [1]
  * environment Grams and A assembly, [2] Jacobi, [3] choice/truncation,
  * [4] BF16 split of T, [5] prime-side chain, [6] bottleneck GEMM, [7]
- * non-prime chain, [8] trace / normalisation; *n = 9.  launches[k] = number
+ * non-prime chain, [8] trace / normalisation, [9] FP32 warm start of the
+ * eigen-solver (included in [2]), [10] its FP32 sweeps (included in [9]);
+ * *n = 11.  launches[k] = number
  * of kernels timed in phase k (the bottleneck: one per c'-slice).
  * *contraction_fp64 = 1 if the last step's contraction ran in FP64. */
 int hotrg_profile(hotrg_ctx* ctx, int enable);
@@ -139,6 +141,9 @@ int hotrg_isometry(hotrg_ctx* ctx, int leg, double* U, int64_t cap, int* rows,
 /* Eigenvalues, descending, of A^(j) (prime = 0) or A'^(j) (prime = 1) for
  * lattice axis `leg` in the last step (Sec. 4.2.5); *n = chi_leg^2. */
 int hotrg_spectrum(hotrg_ctx* ctx, int leg, int prime, double* lam, int64_t cap, int* n);
+
+/* FP64 one-sided Jacobi sweeps used for lattice axis `leg` in the last step. */
+int hotrg_jacobi_sweeps(hotrg_ctx* ctx, int leg, int* sweeps);
 
 /* Discarded sums epsilon^(j), epsilon'^(j) of the last step (Sec. 2). */
 int hotrg_truncation(hotrg_ctx* ctx, int leg, double* eps, double* eps_prime);

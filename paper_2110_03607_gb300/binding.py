@@ -60,6 +60,7 @@ def load():
         "hotrg_isometry": (I, [P, I, P, I64, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "hotrg_spectrum": (I, [P, I, I, P, I64, ctypes.POINTER(I)]),
         "hotrg_truncation": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "hotrg_jacobi_sweeps": (I, [P, I, ctypes.POINTER(I)]),
         "hotrg_free_energy": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hotrg_observables": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
         "hotrg_bond_dims": (I, [P, ctypes.POINTER(I)]),
@@ -153,6 +154,12 @@ def hotrg_truncation(ctx, leg: int):
     return e.value, ep.value
 
 
+def hotrg_jacobi_sweeps(ctx, leg: int) -> int:
+    n = ctypes.c_int()
+    _check(load().hotrg_jacobi_sweeps(ctx, leg, ctypes.byref(n)), "hotrg_jacobi_sweeps")
+    return n.value
+
+
 def hotrg_free_energy(ctx):
     lnz, f = ctypes.c_double(), ctypes.c_double()
     _check(load().hotrg_free_energy(ctx, ctypes.byref(lnz), ctypes.byref(f)), "hotrg_free_energy")
@@ -206,7 +213,7 @@ def hotrg_profile(ctx, enable: bool):
 
 
 PHASES = ["permute", "environment", "jacobi", "select", "split", "prime_chain", "bottleneck",
-          "nonprime_chain", "trace_norm"]
+          "nonprime_chain", "trace_norm", "jacobi_warm_start", "jacobi_fp32"]
 
 
 def hotrg_step_times(ctx):

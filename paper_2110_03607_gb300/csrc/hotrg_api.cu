@@ -637,7 +637,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   CHECK_ALLOC(dev_alloc(c, c->J32, sizeof(float) * 2 * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Gns, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Vtmp, sizeof(double) * total_mat_elems));
-  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * 3 * 2 * kMaxD));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (3 * 2 * kMaxD + 3)));
   CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 2 * kMaxD));
 
   for (int j = 1; j < d; ++j) {
@@ -698,13 +698,20 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     const double* Ag = (const double*)c->Amat.p + base;
     const double* Ainit = Ag;
     if (n >= 32) {
+      Phase phw(c, 9);
       // FP32 warm start, FP64 re-orthonormalisation of its vectors (two Newton-Schulz
       // steps Q <- Q (3I - Q^T Q) / 2), W = A Q; the FP64 sweeps then start from (W, Q)
       float* W32 = (float*)c->J32.p;
       float* V32 = W32 + cnt * nn;
       double* G = (double*)c->Gns.p;
       double* Vt = (double*)c->Vtmp.p;
-      if (launch_jacobi32(Ag, W32, V32, n, cnt, 40, s) == 0) {
+      int ok32;
+      {
+        Phase ph32(c, 10);
+        ok32 = launch_jacobi32_block(Ag, W32, V32, n, cnt, 30, (int*)c->counters.p + 3 * 2 * kMaxD, s) == 0;
+        if (!ok32) cudaGetLastError();
+      }
+      if (ok32) {
         launch_widen_f32(V32, Vg, cnt * nn, s);
         for (int it = 0; it < 2; ++it) {
           launch_gemm_nt_f64_batched(Vg, n, Vg, n, G, n, n, n, n, cnt, nn, nn, nn, s);
@@ -740,7 +747,8 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     // select_kernel addresses matrices 2*leg_index, 2*leg_index+1 from a base
     launch_select((const double*)c->W.p + mat_elem_off[2 * j], (const double*)c->V.p + mat_elem_off[2 * j],
                   n, 0, nnew[j], (double*)c->lam.p + lam_off[j], (double*)c->U64.p + u_off[j],
-                  (float*)c->U32.p + u_off[j], (LegResult*)c->legres.p + j, nullptr, s);
+                  (float*)c->U32.p + u_off[j], (LegResult*)c->legres.p + j,
+                  (int*)c->sweeps.p + (mat_of_leg[j] - grp_first_mat[grp_of[j]]), s);
   }
 
   // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
@@ -975,6 +983,19 @@ int hotrg_spectrum(hotrg_ctx* c, int leg, int prime, double* lam, int64_t cap, i
   return HOTRG_OK;
 }
 
+int hotrg_jacobi_sweeps(hotrg_ctx* c, int leg, int* sweeps) {
+  if (!c || !sweeps) return HOTRG_EINVAL;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  int j = find_leg(c, leg);
+  if (j < 0) return c->last_valid ? HOTRG_EINVAL : HOTRG_ESTATE;
+  LegResult lr;
+  if (cudaMemcpy(&lr, (LegResult*)c->legres.p + (j + 1), sizeof(lr), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_status(c);
+  *sweeps = lr.sweeps[0];
+  return HOTRG_OK;
+}
+
 int hotrg_truncation(hotrg_ctx* c, int leg, double* eps, double* eps_prime) {
   if (!c) return HOTRG_EINVAL;
   int r = sync_and_status(c, nullptr);
@@ -1123,7 +1144,7 @@ int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int*
     ms[m.first] += t;
     if (launches) launches[m.first] += 1;
   }
-  if (n) *n = 9;
+  if (n) *n = 11;
   if (contraction_fp64) *contraction_fp64 = c->last_fp64;
   return HOTRG_OK;
 }

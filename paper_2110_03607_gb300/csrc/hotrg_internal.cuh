@@ -76,8 +76,8 @@ void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int 
 // ---- kernels_eig.cu
 int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
                   int* counters, int* sweeps_out, DevState* st, cudaStream_t s);
-int launch_jacobi32(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
-                    cudaStream_t s);
+int launch_jacobi32_block(const double* A, float* W32, float* V32, int n, int nmat,
+                          int max_sweeps, int* counters, cudaStream_t s);
 void launch_widen_f32(const float* in, double* out, long long n, cudaStream_t s);
 void launch_ns_coeff(double* G, int n, int nmat, cudaStream_t s);
 void launch_gemm_nn_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
@@ -88,7 +88,7 @@ void launch_gemm_nt_f64_batched(const double* A, long long lda, const double* B,
                                 long long bsa, long long bsb, long long bsc, cudaStream_t s);
 void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
                    double* lam_sorted, double* U64, float* U32, LegResult* res,
-                   int* scratch_order, cudaStream_t s);
+                   const int* sweeps, cudaStream_t s);
 
 // ---- kernels_chain.cu
 void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U,

@@ -166,83 +166,141 @@ int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int ma
 }
 
 // ---------------------------------------------------------------------------
-// FP32 warm start: the same one-sided Jacobi in single precision, one CTA per
-// matrix (rounds separated by __syncthreads, no grid barrier).  Its vectors
-// only seed the FP64 sweeps, which restore full accuracy; it stops at FP32
-// tolerance or after max_sweeps without raising an error.
+// FP32 warm start: block one-sided Jacobi.  The n columns of W = A V are cut
+// into nb blocks of b; an outer round pairs the blocks round-robin and one CTA
+// per block pair loads its 2b columns of W and V into shared memory, runs one
+// inner sweep of one-sided Jacobi over them (2b-1 inner rounds of b disjoint
+// pairs, separated by __syncthreads), and writes them back.  Outer rounds are
+// separated by a grid barrier of a cooperative launch, so a sweep costs nb-1
+// grid barriers instead of n-1.  Its vectors only seed the FP64 sweeps, which
+// restore full accuracy; it stops when an outer sweep rotates nothing, or after
+// max_sweeps, without raising an error.
 // ---------------------------------------------------------------------------
 template <int NPL>
-__global__ void __launch_bounds__(1024) jacobi32_kernel(const double* __restrict__ A, float* W,
-                                                        float* V, int n, int max_sweeps) {
+__global__ void __launch_bounds__(1024) jacobi32_block_kernel(const double* __restrict__ A, float* W,
+                                                              float* V, int n, int b, int nb,
+                                                              int nmat, int max_sweeps, int* counters) {
+  extern __shared__ float jsm[];
   __shared__ int s_rot;
+  cg::grid_group grid = cg::this_grid();
   const long long nn = (long long)n * n;
-  float* Wm = W + blockIdx.x * nn;
-  float* Vm = V + blockIdx.x * nn;
-  const double* Am = A + blockIdx.x * nn;
-  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-    Wm[e] = (float)Am[e];
-    Vm[e] = (e / n == e % n) ? 1.0f : 0.0f;
+  const int kpairs = nb / 2;
+  const int mat = blockIdx.x / kpairs, kp = blockIdx.x % kpairs;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gthreads = (long long)gridDim.x * blockDim.x;
+  for (long long e = gtid; e < (long long)nmat * nn; e += gthreads) {
+    long long r = e % nn;
+    W[e] = (float)A[e];
+    V[e] = (r / n == r % n) ? 1.0f : 0.0f;
   }
-  const int mp = n + (n & 1), npairs = mp / 2, rounds = mp - 1;
+  if (gtid < 3) counters[gtid] = 0;
+  grid.sync();
+  float* Wm = W + mat * nn;
+  float* Vm = V + mat * nn;
+  float* sw = jsm;                          // [2b][n]
+  float* sv = jsm + (long long)2 * b * n;   // [2b][n]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float tol = 4.0f * (float)n * 1.1920929e-7f;
+  const int m2 = 2 * b;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < rounds; ++r) {
-      for (int k = warp; k < npairs; k += nw) {
-        int p = rr_slot(k, r, mp), q = rr_slot(mp - 1 - k, r, mp);
-        if (p >= n || q >= n) continue;
-        if (p > q) { int t = p; p = q; q = t; }
-        float* wp = Wm + (long long)p * n;
-        float* wq = Wm + (long long)q * n;
-        float xs[NPL], ys[NPL];
-        float a = 0.f, b = 0.f, g = 0.f;
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-          int i = lane + 32 * u;
-          float x = i < n ? wp[i] : 0.f, y = i < n ? wq[i] : 0.f;
-          xs[u] = x;
-          ys[u] = y;
-          a = fmaf(x, x, a);
-          b = fmaf(y, y, b);
-          g = fmaf(x, y, g);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        if (g == 0.f || !(fabsf(g) > tol * sqrtf(a * b))) continue;
-        float zeta = (b - a) / (2.f * g);
-        float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-          int i = lane + 32 * u;
-          if (i < n) {
-            wp[i] = c * xs[u] - sn * ys[u];
-            wq[i] = sn * xs[u] + c * ys[u];
-          }
-        }
-        float* vp = Vm + (long long)p * n;
-        float* vq = Vm + (long long)q * n;
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-          int i = lane + 32 * u;
-          if (i < n) {
-            float x = vp[i], y = vq[i];
-            vp[i] = c * x - sn * y;
-            vq[i] = sn * x + c * y;
-          }
-        }
-        if (lane == 0) atomicAdd(&s_rot, 1);
+    int* cur = counters + (sweep % 3);
+    if (gtid == 0) counters[(sweep + 1) % 3] = 0;
+    for (int r = 0; r < nb - 1; ++r) {
+      const int bi = rr_slot(kp, r, nb), bj = rr_slot(nb - 1 - kp, r, nb);
+      // local column c < b is block bi's column, c >= b block bj's
+      for (long long e = threadIdx.x; e < (long long)m2 * n; e += blockDim.x) {
+        int c = (int)(e / n), i = (int)(e % n);
+        int gc = (c < b ? bi * b + c : bj * b + (c - b));
+        bool in = gc < n;
+        sw[e] = in ? Wm[(long long)gc * n + i] : 0.0f;
+        sv[e] = in ? Vm[(long long)gc * n + i] : 0.0f;
       }
+      if (threadIdx.x == 0) s_rot = 0;
       __syncthreads();
+      for (int ir = 0; ir < m2 - 1; ++ir) {
+        for (int k = warp; k < b; k += nw) {
+          int p = rr_slot(k, ir, m2), q = rr_slot(m2 - 1 - k, ir, m2);
+          if (p > q) { int t = p; p = q; q = t; }
+          float* wp = sw + (long long)p * n;
+          float* wq = sw + (long long)q * n;
+          float xs[NPL], ys[NPL];
+          float a = 0.f, bb = 0.f, g = 0.f;
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            int i = lane + 32 * u;
+            float x = i < n ? wp[i] : 0.f, y = i < n ? wq[i] : 0.f;
+            xs[u] = x;
+            ys[u] = y;
+            a = fmaf(x, x, a);
+            bb = fmaf(y, y, bb);
+            g = fmaf(x, y, g);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+          }
+          if (g == 0.f || !(fabsf(g) > tol * sqrtf(a * bb))) continue;
+          float zeta = (bb - a) / (2.f * g);
+          float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
+          float* vp = sv + (long long)p * n;
+          float* vq = sv + (long long)q * n;
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            int i = lane + 32 * u;
+            if (i < n) {
+              wp[i] = c * xs[u] - sn * ys[u];
+              wq[i] = sn * xs[u] + c * ys[u];
+              float x = vp[i], y = vq[i];
+              vp[i] = c * x - sn * y;
+              vq[i] = sn * x + c * y;
+            }
+          }
+          if (lane == 0) atomicAdd(&s_rot, 1);
+        }
+        __syncthreads();
+      }
+      for (long long e = threadIdx.x; e < (long long)m2 * n; e += blockDim.x) {
+        int c = (int)(e / n), i = (int)(e % n);
+        int gc = (c < b ? bi * b + c : bj * b + (c - b));
+        if (gc < n) {
+          Wm[(long long)gc * n + i] = sw[e];
+          Vm[(long long)gc * n + i] = sv[e];
+        }
+      }
+      if (threadIdx.x == 0 && s_rot) atomicAdd(cur, s_rot);
+      grid.sync();
     }
-    if (s_rot == 0) break;
-    __syncthreads();
+    if (__ldcg(cur) == 0) break;
   }
+}
+
+// Block size b (nb = ceil(n / b) even, 2b <= 64 pairs of warps) so that two
+// blocks of W and V fit in 200 KB of shared memory.
+int launch_jacobi32_block(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
+                          int* counters, cudaStream_t s) {
+  int b = 32;
+  while (b > 4 && (size_t)4 * b * n * sizeof(float) > 200 * 1024) b /= 2;
+  int nb = (n + b - 1) / b;
+  if (nb & 1) ++nb;
+  if (nb < 2) nb = 2;
+  size_t smem = (size_t)4 * b * n * sizeof(float);
+  if (smem > 200 * 1024) return -1;
+  int npl = (n + 31) / 32;
+  void* kern = nullptr;
+  if (npl <= 2) kern = (void*)jacobi32_block_kernel<2>;
+  else if (npl <= 4) kern = (void*)jacobi32_block_kernel<4>;
+  else if (npl <= 8) kern = (void*)jacobi32_block_kernel<8>;
+  else if (npl <= 16) kern = (void*)jacobi32_block_kernel<16>;
+  else return -1;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  int blocks = nmat * (nb / 2);
+  void* args[] = {&A, &W32, &V32, &n, &b, &nb, &nmat, &max_sweeps, &counters};
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(1024), args, smem, s);
+  ++g_launches;
+  return e == cudaSuccess ? 0 : -1;
 }
 
 // Q = V32 in FP64, and 0.5 (3 I - G) for the Newton-Schulz step Q <- Q (3I - Q^T Q) / 2
@@ -259,19 +317,6 @@ __global__ void ns_coeff_kernel(double* G, int n, long long total) {
     int i = (int)(r / n), j = (int)(r % n);
     G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
   }
-}
-
-int launch_jacobi32(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
-                    cudaStream_t s) {
-  int npl = (n + 31) / 32;
-  if (npl <= 2) jacobi32_kernel<2><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
-  else if (npl <= 4) jacobi32_kernel<4><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
-  else if (npl <= 8) jacobi32_kernel<8><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
-  else if (npl <= 16) jacobi32_kernel<16><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
-  else if (npl <= 32) jacobi32_kernel<32><<<nmat, 1024, 0, s>>>(A, W32, V32, n, max_sweeps);
-  else return -1;
-  ++g_launches;
-  return 0;
 }
 
 void launch_widen_f32(const float* in, double* out, long long n, cudaStream_t s) {
@@ -302,7 +347,8 @@ void launch_ns_coeff(double* G, int n, int nmat, cudaStream_t s) {
 __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ W,
                                                      const double* __restrict__ V, int n,
                                                      int leg_index, int nnew, double* lam_sorted,
-                                                     double* U64, float* U32, LegResult* res) {
+                                                     double* U64, float* U32, LegResult* res,
+                                                     const int* sweeps) {
   extern __shared__ double sm[];
   double* lam = sm;                         // [2][n]
   int* piv = (int*)(lam + 2 * n);           // [2][n]
@@ -390,6 +436,8 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
     res->lam1[0] = l1a;
     res->lam1[1] = l1b;
     res->chose_prime = prime;
+    res->sweeps[0] = sweeps ? sweeps[0] : 0;
+    res->sweeps[1] = sweeps ? sweeps[1] : 0;
     res->gap = (nnew < n && lc[oc[0]] > 0.0) ? (lc[oc[nnew - 1]] - lc[oc[nnew]]) / lc[oc[0]] : 1e300;
   }
   __syncthreads();
@@ -410,12 +458,11 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
 
 void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
                    double* lam_sorted, double* U64, float* U32, LegResult* res,
-                   int* scratch_order, cudaStream_t s) {
-  (void)scratch_order;
+                   const int* sweeps, cudaStream_t s) {
   size_t smem = (size_t)2 * n * sizeof(double) + (size_t)6 * n * sizeof(int);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  select_kernel<<<1, 512, smem, s>>>(W, V, n, leg_index, nnew, lam_sorted, U64, U32, res);
+  select_kernel<<<1, 512, smem, s>>>(W, V, n, leg_index, nnew, lam_sorted, U64, U32, res, sweeps);
   ++g_launches;
 }
 
