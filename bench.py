@@ -1,14 +1,16 @@
-"""Benchmark: 3D Ising HOTRG, chi = 16, steps/s on one GB300 (per rank).
+"""Benchmark: HOTRG coarse-graining steps/s on one GB300 (per rank).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|fp64]
-                    [--impl ours|reference]
+                    [--workload ising3d_chi16|ising3d_chi20|ising4d_chi6] [--impl ours|reference]
 
-Workload: d = 3, chi = 16, beta = 0.2216544, h = 0, axes cycling z, x, y.  The
-first three steps grow the bonds 2 -> 4 -> 16 and are not timed; then W
-steady-state warm-up steps and K timed steps, each one full coarse-graining
-(permutation, FP64 environments, Jacobi, choice/truncation, prime chain,
-bottleneck, non-prime chain, trace/normalisation).  The local tensor (134 MB
-FP64) and the per-slice operands (GBs) exceed the 129 MB L2.
+Default workload: 3D Ising, d = 3, chi = 16, beta = 0.2216544, h = 0, axes cycling
+z, x, y.  The first steps grow the bonds (2 -> 4 -> 16 for the default) and are not
+timed; then W steady-state warm-up steps and K timed steps, each one full
+coarse-graining (permutation, FP64 environments, Jacobi, choice/truncation, prime
+chain, bottleneck, non-prime chain, trace/normalisation).  The local tensor (134 MB
+FP64 for the default) and the per-slice operands (GBs) exceed the 129 MB L2.
+Per-step ln Z/V is compared with the FP64 oracle's reference values in
+tests/golden/<workload>.jsonl where those exist.
 
 Multi-GPU: independent replicas (one run per rank), weak scaling, no
 collective on the data path; rank 0 prints one JSON line.
@@ -29,11 +31,30 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-D, CHI, BETA, H = 3, 16, 0.2216544, 0.0
-FIRST_AXIS = 2          # z, then x, y
-GROWTH_STEPS = 3
-WORKLOAD = "ising3d_chi16"
 METRIC = "3D-Ising chi=16 HOTRG steps/s, split-BF16 vs FP64, rel err in f<=1e-7; TFLOP/s"
+
+# workload -> lattice dimension, bond dimension, coupling, field, first axis, the number of
+# bond-growth steps before every bond reaches chi (not timed), and a description
+WORKLOADS = {
+    "ising3d_chi16": dict(d=3, chi=16, beta=0.2216544, h=0.0, first=2, growth=3,
+                          text="3D Ising HOTRG d=3 chi=16 beta=0.2216544 h=0, axes z,x,y"),
+    "ising3d_chi20": dict(d=3, chi=20, beta=0.2216544, h=0.0, first=2, growth=5,
+                          text="3D Ising HOTRG d=3 chi=20 beta=0.2216544 h=0, axes z,x,y"),
+    "ising4d_chi6": dict(d=4, chi=6, beta=0.15, h=0.0, first=0, growth=3,
+                         text="4D Ising HOTRG d=4 chi=6 beta=0.15 h=0, axes x,y,z,w"),
+}
+W = dict(WORKLOADS["ising3d_chi16"])
+WORKLOAD = "ising3d_chi16"
+D, CHI, BETA, H = W["d"], W["chi"], W["beta"], W["h"]
+FIRST_AXIS, GROWTH_STEPS = W["first"], W["growth"]
+
+
+def select_workload(name):
+    global W, WORKLOAD, D, CHI, BETA, H, FIRST_AXIS, GROWTH_STEPS
+    W = dict(WORKLOADS[name])
+    WORKLOAD = name
+    D, CHI, BETA, H = W["d"], W["chi"], W["beta"], W["h"]
+    FIRST_AXIS, GROWTH_STEPS = W["first"], W["growth"]
 
 
 def axes_for(n):
@@ -164,7 +185,7 @@ def cpu_baseline_leg():
     run = oracle_steady_tensor()
     est, info = oracle_step_sample(run, axes_for(GROWTH_STEPS + 1)[-1], 48)
     return {"value": 1.0 / est, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one steady-state 3D chi=16 step: environments + Jacobi in full "
+            "sample": (f"one steady-state step of {W['text']}: environments + Jacobi in full "
                        f"({info['env_eig_s']} s), {info['contraction_iters_timed']} of "
                        f"{info['contraction_iters_total']} (c'_0, n') contraction iterations, "
                        f"extrapolated to the whole step"),
@@ -187,11 +208,11 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * mean, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D Ising HOTRG d=3 chi=16 beta=0.2216544 h=0, axes z,x,y",
-                       "sample": "each step: oracle environments + Jacobi in full and 16 of 4096 "
+            "config": {"workload": W["text"],
+                       "sample": "each step: oracle environments + Jacobi in full and 16 "
                                  "contraction iterations, extrapolated"},
             "cpu_baseline": {"value": 1.0 / mean, "unit": "steps/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": "16 of 4096 contraction iterations per step"},
+                             "kind": "oracle", "sample": "16 contraction iterations per step, extrapolated"},
             "e2e": {"value": 1.0 / mean, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -211,7 +232,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    select_workload(args.workload)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -284,7 +307,7 @@ def main():
     rel_err = max(errs.values()) if errs else None
 
     # ---- roofline of the bottleneck GEMM (algorithmic flops per c'-slice launch)
-    R = CHI ** D                   # rows = cols of T at steady state
+    R = CHI ** D                   # rows = cols of T at steady state (all bonds chi)
     Ns = CHI ** (2 * (D - 1))      # (n', n~) columns per c'-slice
     flops_per_launch = 2.0 * R * R * Ns
     peaks, peak_src = load_peaks()
@@ -335,7 +358,7 @@ def main():
     g.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD != "ising3d_chi20":
         cpu = cpu_baseline_leg()
 
     if rank == 0:
@@ -348,14 +371,15 @@ def main():
                       "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic (Ising initial tensor from beta, h; no dataset)",
-            "config": {"workload": "3D Ising HOTRG d=3 chi=16 beta=0.2216544 h=0, axes z,x,y; "
-                                   f"steps 1-3 (bond growth) untimed, {args.warmup} warm-up steps, "
+            "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
+                                   f"{args.warmup} warm-up steps, "
                                    f"steps {GROWTH_STEPS + args.warmup + 1}-{GROWTH_STEPS + args.warmup + K} timed",
                        "precision": args.precision, "l2": "inputs larger than L2 (T 134 MB, "
                                                           "per-slice operands GBs)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "rel_err_lnz_per_site_vs_oracle": rel_err,
             "rel_err_steps_compared": len(errs),
+            "rel_err_by_step": {str(k): v for k, v in sorted(errs.items())},
             "phases_ms_per_step": mean_phase,
             "roofline": roof,
             "e2e": e2e,
