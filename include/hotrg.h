@@ -105,6 +105,13 @@ int hotrg_set_precision(hotrg_ctx* ctx, int mode);
  * in step p weighs 2^-p in ln Z / V).  Default 2^36; 0 = never. */
 int hotrg_set_fp64_threshold(hotrg_ctx* ctx, double flops);
 
+/* Cap, in bytes, on the device memory of the per-slice contraction operands
+ * (bottleneck operand pieces, its FP32 product, chain intermediates).  Each
+ * c'-slice of the new-tensor contraction (Sec. 4.2.9) is further cut into
+ * sub-ranges of n'_1 so that one sub-range fits the smaller of this cap and
+ * 60 % of the free device memory.  Default 160e9. */
+int hotrg_set_slice_budget(hotrg_ctx* ctx, double bytes);
+
 /* Record CUDA events around the phases of every later step (enable = 1) or
  * stop (0).  hotrg_step_times() then returns, after synchronising, the
  * milliseconds of the last step per phase: [0] leg permutation, [1]

@@ -67,6 +67,7 @@ def load():
         "hotrg_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
         "hotrg_gemm_nt": (I, [I, I, I, I, P, P, P]),
         "hotrg_set_fp64_threshold": (I, [P, D]),
+        "hotrg_set_slice_budget": (I, [P, D]),
         "hotrg_profile": (I, [P, I]),
         "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -206,6 +207,10 @@ def hotrg_gemm_nt(mode: int, a, b):
 
 def hotrg_set_fp64_threshold(ctx, flops: float):
     _check(load().hotrg_set_fp64_threshold(ctx, float(flops)), "hotrg_set_fp64_threshold")
+
+
+def hotrg_set_slice_budget(ctx, nbytes: float):
+    _check(load().hotrg_set_slice_budget(ctx, float(nbytes)), "hotrg_set_slice_budget")
 
 
 def hotrg_profile(ctx, enable: bool):

@@ -112,6 +112,7 @@ bool make_stage(ChainDesc& d, const View& in, const View& out, int a_name, int b
   d.n_out_stride = stride_of(out, n_name);
   d.chi = chi;
   d.nn = nn;
+  d.ldu = nn;
   d.npieces = 1;
   if (d.total >= (1LL << 32)) return false;
   for (int k = 0; k < d.ndim; ++k) {
@@ -142,6 +143,7 @@ struct hotrg_ctx {
   int poisoned = 0;
   size_t held = 0;
   double fp64_below = 68719476736.0;  // 2^36 flops
+  double slice_budget_bytes = 160e9;   // cap on the per-(sub)slice operands
   // diagnostic: FP64-accumulating chains around the split-BF16 bottleneck
   int f64_chains = getenv("HOTRG_DEBUG_F64_CHAINS") ? atoi(getenv("HOTRG_DEBUG_F64_CHAINS")) : 0;
   // phase timing
@@ -772,18 +774,34 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
   size_t elt = (fp64 || c->f64_chains) ? sizeof(double) : sizeof(float);
-  CHECK_ALLOC(dev_alloc(c, c->chA, elt * chain_max));
-  CHECK_ALLOC(dev_alloc(c, c->chB, elt * chain_max));
+  // Sub-slices of n'_1 keep the per-slice operands within a device-memory budget:
+  // everything below except the split T scales with the number of n'_1 values.
+  const int nnew1 = nnew[1];
+  int n1_chunk = nnew1;
+  {
+    const double per_unit =
+        (double)(Ns / nnew1) * ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
+        2.0 * (double)elt * (double)chain_max / nnew1;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    double budget = std::min(0.6 * (double)free_b + (double)(c->Bp.bytes + c->Cb.bytes + c->chA.bytes + c->chB.bytes),
+                             c->slice_budget_bytes);
+    n1_chunk = (int)std::max(1.0, std::min((double)nnew1, std::floor(budget / per_unit)));
+  }
+  const long long Nsub = (long long)n1_chunk * (Ns / nnew1);
+  const long long chain_sub = (chain_max / nnew1) * n1_chunk;
+  CHECK_ALLOC(dev_alloc(c, c->chA, elt * chain_sub));
+  CHECK_ALLOC(dev_alloc(c, c->chB, elt * chain_sub));
   if (fp64) {
-    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Ns * R));
-    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(double) * R * Ns));
+    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Nsub * R));
+    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(double) * R * Nsub));
   } else {
     CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
-    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Ns * Kpad));
-    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Ns));
+    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
+    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
     if (Kpad != R) {
       cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
-      cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Ns * Kpad, s);
+      cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
     }
     Phase ph(c, 4);
     launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
@@ -814,7 +832,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
 
-  for (int sl = 0; sl < chi_c; ++sl) {
+  for (int sl = 0; sl < chi_c; ++sl)
+  for (int n1lo = 0; n1lo < nnew1; n1lo += n1_chunk) {
+    const int n1cnt = std::min(n1_chunk, nnew1 - n1lo);
+    const long long Nc = (long long)n1cnt * (Ns / nnew1);   // bottleneck columns of this sub-slice
+    int nsz[kMaxD];                                          // n' sizes of this sub-slice
+    for (int k = 1; k < d; ++k) nsz[k] = k == 1 ? n1cnt : nnew[k];
     // -- prime-side chain, Eqs. (TU1)-(TUNCD), on the c'-fixed tensor T[(rho, n~), (sl, n~')]
     View in;
     in.push_back({I_RHO, chi_c, rs[0]});
@@ -828,7 +851,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       bool last = (j == d - 1);
       if (!last) {
         std::vector<std::pair<int, long long>> names;
-        for (int k = 1; k <= j; ++k) names.push_back({I_NP + k, nnew[k]});
+        for (int k = 1; k <= j; ++k) names.push_back({I_NP + k, nsz[k]});
         names.push_back({I_RHO, chi_c});
         for (int k = 1; k < d; ++k) names.push_back({I_NC + k, chij[k]});
         for (int k = j + 1; k < d; ++k) names.push_back({I_NCP + k, chij[k]});
@@ -836,28 +859,31 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         out = contiguous(names);
       } else {
         long long K_ = Kpad;
-        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nnew[k], prod_after(nnew, k) * P * K_});
+        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P * K_});
         for (int k = 1; k < d; ++k) out.push_back({I_NC + k, chij[k], prod_after(chij, k) * K_});
         out.push_back({I_RHO, chi_c, P});
         for (int k = 1; k < d; ++k) out.push_back({I_NHP + k, chij[k], prod_after(chij, k)});
       }
       ChainDesc cd;
-      if (!make_stage(cd, in, out, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nnew[j])) {
+      if (!make_stage(cd, in, out, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nsz[j])) {
         c->poisoned = HOTRG_EINVAL;
         return HOTRG_EINVAL;
       }
+      // columns n1lo .. n1lo + n1cnt - 1 of U~^(1) give this sub-slice's n'_1
+      cd.ldu = nnew[j];
+      const long long ucol = j == 1 ? n1lo : 0;
       void* dst = last ? c->Bp.p : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
-        launch_chain_f64(cd, (const double*)src, (const double*)c->U64.p + u_off[j], (double*)dst, s);
+        launch_chain_f64(cd, (const double*)src, (const double*)c->U64.p + u_off[j] + ucol, (double*)dst, s);
       } else if (c->f64_chains) {
         cd.npieces = npieces;
-        cd.piece_stride = Ns * Kpad;
-        launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j], dst,
+        cd.piece_stride = Nc * Kpad;
+        launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j] + ucol, dst,
                             last ? OUT_BF16_SPLIT : OUT_F64, s);
       } else {
         cd.npieces = npieces;
-        cd.piece_stride = Ns * Kpad;
-        launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j], dst,
+        cd.piece_stride = Nc * Kpad;
+        launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, dst,
                          last ? OUT_BF16_SPLIT : OUT_F32, s);
       }
       src = dst;
@@ -868,20 +894,20 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     {
     Phase ph(c, 6);
     if (fp64) {
-      launch_gemm_nt_f64(Tc, R, (const double*)c->Bp.p, R, (double*)c->Cb.p, Ns, 0, (int)R, (int)Ns,
+      launch_gemm_nt_f64(Tc, R, (const double*)c->Bp.p, R, (double*)c->Cb.p, Nc, 0, (int)R, (int)Nc,
                          R, 1, 0, s);
     } else {
-      if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Ns,
-                         (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Ns,
+      if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
+                         (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Nc,
                          &((DevState*)c->state.p)->status, s, nullptr) != 0)
         return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
     }
     }
     // -- non-prime chain, Eqs. (AfterBNNCD)-(AfterBN1), Eq. (Elements_NewTensor)
     View cin;
-    cin.push_back({I_C, chi_c, P * Ns});
-    for (int k = 1; k < d; ++k) cin.push_back({I_NH + k, chij[k], prod_after(chij, k) * Ns});
-    for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nnew[k], prod_after(nnew, k) * P});
+    cin.push_back({I_C, chi_c, P * Nc});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NH + k, chij[k], prod_after(chij, k) * Nc});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P});
     for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
     const void* csrc = c->Cb.p;
     for (int j = d - 1; j >= 1; --j) {
@@ -892,21 +918,22 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         std::vector<std::pair<int, long long>> names;
         names.push_back({I_C, chi_c});
         for (int k = 1; k < j; ++k) names.push_back({I_NH + k, chij[k]});
-        for (int k = 1; k < d; ++k) names.push_back({I_NP + k, nnew[k]});
+        for (int k = 1; k < d; ++k) names.push_back({I_NP + k, nsz[k]});
         for (int k = 1; k < j; ++k) names.push_back({I_NC + k, chij[k]});
         for (int k = j; k < d; ++k) names.push_back({I_N + k, nnew[k]});
         out = contiguous(names);
       } else {
         out.push_back({I_C, chi_c, Pn * Rn});
         for (int k = 1; k < d; ++k) out.push_back({I_N + k, nnew[k], prod_after(nnew, k) * Rn});
-        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nnew[k], prod_after(nnew, k)});
+        for (int k = 1; k < d; ++k) out.push_back({I_NP + k, nsz[k], prod_after(nnew, k)});
       }
       ChainDesc cd;
       if (!make_stage(cd, cin, out, I_NH + j, I_NC + j, I_N + j, chij[j], nnew[j])) {
         c->poisoned = HOTRG_EINVAL;
         return HOTRG_EINVAL;
       }
-      void* dst = last ? (void*)(Tn + (long long)sl * Pn) : ((j & 1) ? c->chA.p : c->chB.p);
+      void* dst = last ? (void*)(Tn + (long long)sl * Pn + (long long)n1lo * prod_after(nnew, 1))
+                       : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
         launch_chain_f64(cd, (const double*)csrc, (const double*)c->U64.p + u_off[j], (double*)dst, s);
       } else if (c->f64_chains) {
@@ -1121,6 +1148,12 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
 int hotrg_set_fp64_threshold(hotrg_ctx* c, double flops) {
   if (!c || !(flops >= 0.0)) return HOTRG_EINVAL;
   c->fp64_below = flops;
+  return HOTRG_OK;
+}
+
+int hotrg_set_slice_budget(hotrg_ctx* c, double bytes) {
+  if (!c || !(bytes >= 0.0)) return HOTRG_EINVAL;
+  c->slice_budget_bytes = bytes;
   return HOTRG_OK;
 }
 

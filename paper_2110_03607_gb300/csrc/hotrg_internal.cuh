@@ -41,7 +41,8 @@ struct ChainDesc {
   int ndim;
   int a_dim;
   int chi;             // chi_j (U has chi*chi rows)
-  int nn;              // chi_j^new (U columns)
+  int nn;              // U columns used
+  int ldu;             // row stride of U (>= nn)
   long long size[kMaxDims];
   long long in_stride[kMaxDims];
   long long out_stride[kMaxDims];

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
   const int ld = NN + 1;
   for (int e = threadIdx.x; e < rows * NN; e += blockDim.x) {
     int r = e / NN, c = e % NN;
-    us[r * ld + c] = c < d.nn ? U[r * d.nn + c] : TAcc(0);
+    us[r * ld + c] = c < d.nn ? U[r * d.ldu + c] : TAcc(0);
   }
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;

@@ -111,6 +111,25 @@ def test_default_policy_keeps_early_steps_exact(pkg):
         assert abs(lnz - exact) / abs(exact) <= 1e-12
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (2, 5e-7)])
+@pytest.mark.parametrize("d,chi,nsteps", [(3, 5, 6), (4, 3, 5), (2, 6, 8)])
+def test_n1_sub_slices_match_oracle(pkg, prec, tol, d, chi, nsteps):
+    # a 1-byte budget forces one n'_1 value per sub-slice of every c'-slice
+    beta, h = 0.25, 0.03
+    axes = o.cyclic_axes(d, nsteps)
+    g = pkg.Hotrg(d, beta, h, precision=prec, fp64_below=0.0)
+    run = o.HotrgRun(d, beta, h)
+    try:
+        pkg.hotrg_set_slice_budget(g.ctx, 1.0)
+        for a in axes:
+            g.step(a, chi)
+            rec = run.step(a, chi)
+            lnz, _ = g.free_energy()
+            assert abs(lnz - rec.ln_z_per_site) / abs(rec.ln_z_per_site) <= tol, (rec.step, lnz)
+    finally:
+        g.close()
+
+
 def test_beta_zero_gives_ln2(pkg):
     res = _gpu_run(pkg, 3, 0.0, 0.0, 4, o.cyclic_axes(3, 5), 2)
     for lnz, _, _ in res:
