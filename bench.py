@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
+    ap.add_argument("--z2", default="on", choices=["on", "off"],
+                    help="Z2 block form of the contraction (on) or the paper's dense form (off)")
     args = ap.parse_args()
     select_workload(args.workload)
     if args.warmup < 3 and not args.workload.startswith("ising4d_chi1"):
@@ -260,7 +262,7 @@ def main():
     prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
     stream = torch.cuda.current_stream()
 
-    g = pkg.Hotrg(D, BETA, H, precision=prec)
+    g = pkg.Hotrg(D, BETA, H, precision=prec, z2=args.z2 == "on")
     axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
     lnz_by_step = {}
     for i, a in enumerate(axes[: GROWTH_STEPS + args.warmup]):
@@ -273,6 +275,8 @@ def main():
     sampler.start()
     time.sleep(0.3)
     phase_sum, launch_sum = {}, {}
+    bn_dense = bn_done = 0.0
+    z2_steps = 0
     launches0 = pkg.hotrg_launch_count(g.ctx)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -290,6 +294,10 @@ def main():
         for k, v in ms.items():
             phase_sum[k] = phase_sum.get(k, 0.0) + v
             launch_sum[k] = launch_sum.get(k, 0) + nl[k]
+        fd, fp, zb = pkg.hotrg_bottleneck_flops(g.ctx)
+        bn_dense += fd
+        bn_done += fp
+        z2_steps += int(zb)
         lnz_by_step[step_no] = g.free_energy()[0]
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -311,13 +319,13 @@ def main():
     errs = {s: abs(lnz_by_step[s] - golden[s]) / abs(golden[s]) for s in lnz_by_step if s in golden}
     rel_err = max(errs.values()) if errs else None
 
-    # ---- roofline of the bottleneck GEMM (algorithmic flops per c'-slice launch)
-    R = CHI ** D                   # rows = cols of T at steady state (all bonds chi)
-    Ns = CHI ** (2 * (D - 1))      # (n', n~) columns per c'-slice
-    flops_per_launch = 2.0 * R * R * Ns
+    # ---- roofline of the bottleneck GEMM: algorithmic flops per launch (dense: one
+    # launch of 2 R^2 Ns per c'-slice; Z2 blocks: two launches per c'-slice whose
+    # flops, padding excluded, the library reports) / CUDA-event time per launch
     peaks, peak_src = load_peaks()
     bn_launches = launch_sum.get("bottleneck", 0)
     bn_ms = phase_sum.get("bottleneck", 0.0) / max(1, bn_launches)
+    flops_per_launch = bn_done / max(1, bn_launches)
     nterms = {"bf16x6": 6, "bf16x3": 3, "fp64": 1}[args.precision]
     achieved = flops_per_launch / (bn_ms / 1000.0) / 1e12 if bn_ms > 0 else None
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
@@ -332,7 +340,10 @@ def main():
                 "issued_tflops": achieved * nterms if achieved else None,
                 "issued_frac": achieved * nterms / peak if achieved else None,
                 "algorithmic_flops_per_launch": flops_per_launch,
-                "avg_launch_ms": bn_ms}
+                "avg_launch_ms": bn_ms,
+                "launches_per_step": bn_launches / K,
+                "dense_equivalent_tflops": (bn_dense / K) / (phase_sum.get("bottleneck", 0.0) / K / 1000.0)
+                / 1e12 if bn_launches else None}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -348,10 +359,15 @@ def main():
         t0 = time.perf_counter()
         h2d = d2h = 0
         chis = pkg.hotrg_bond_dims(g.ctx)[:D]
+        parity = pkg.hotrg_leg_parity(g.ctx)
         for a in e2e_axes:
             pkg.hotrg_set_tensor(g.ctx, chis, pinned)      # host -> device
             h2d += pinned.numel() * 8
+            if parity is not None:                         # declared leg parities (Z2)
+                pkg.hotrg_set_parity(g.ctx, parity)
+                h2d += 4 * len(parity)
             g.step(a, CHI)
+            parity = pkg.hotrg_leg_parity(g.ctx)
             pkg.hotrg_free_energy(g.ctx)                    # 16-byte read-back
             pkg.hotrg_tensor(g.ctx, out.numpy().reshape([c for c in chis for _ in (0, 1)]))
             d2h += out.numel() * 8 + 16
@@ -379,8 +395,11 @@ def main():
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, "
                                    f"steps {GROWTH_STEPS + args.warmup + 1}-{GROWTH_STEPS + args.warmup + K} timed",
-                       "precision": args.precision, "l2": "inputs larger than L2 (T 134 MB, "
-                                                          "per-slice operands GBs)",
+                       "precision": args.precision,
+                       "z2_blocks": args.z2 == "on",
+                       "z2_steps_timed": z2_steps,
+                       "bottleneck_flops_per_step": {"dense": bn_dense / K, "performed": bn_done / K},
+                       "l2": "inputs larger than L2 (T 134 MB, per-slice operands GBs)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "rel_err_lnz_per_site_vs_oracle": rel_err,
             "rel_err_steps_compared": len(errs),

@@ -16,7 +16,10 @@
  *    outputs go through out-pointers.  hotrg_strerror() names a status.
  *  - The library owns all device memory of a context.  It allocates with
  *    cudaMalloc, or through the hook given to hotrg_set_allocator().
- *  - hotrg_step() only enqueues work on the context's stream and returns.
+ *  - hotrg_step() only enqueues work on the context's stream and returns,
+ *    except that while the leg parities are known (hotrg_set_z2) it waits
+ *    once per step for the isometries, whose column parities give the new
+ *    legs' parities and shape the Z2 block form of the contraction.
  *    The read-back calls (hotrg_free_energy, hotrg_observables,
  *    hotrg_isometry, hotrg_spectrum, hotrg_tensor) synchronise that stream.
  *  - Device-side failures (a non-positive or non-finite trace, a Jacobi
@@ -71,7 +74,10 @@ enum hotrg_precision {
  * normalised by f^(0) = 1/Tr T (Sec. 4.2.1) and ln Z^(0) = ln Tr T^(0).
  * d in [2, 4]; beta >= 0 (beta = 0 allowed; sqrt(sinh beta) is imaginary
  * for beta < 0).  On success *out owns a new context (default stream 0,
- * precision BF16X6).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * precision BF16X6).  At h = 0 the run starts with known leg parities
+ * (index 0 even, index 1 odd; every element of odd total parity is zero) and
+ * the contraction uses the Z2 block form of hotrg_set_z2.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 int hotrg_init_ising(int d, double beta, double h, hotrg_ctx** out);
 
 /* Start a run from a caller-given initial tensor T (interchange layout,
@@ -81,7 +87,8 @@ int hotrg_init_tensor(int d, const int* chis, const double* T, double beta, hotr
 
 /* Replace the current (normalised) local tensor of a run by T with bond
  * dimensions chis, keeping the run's K / ln Z bookkeeping (a resume from a
- * checkpoint).  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
+ * checkpoint).  The leg parities become unknown (see hotrg_set_parity).
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
 int hotrg_set_tensor(hotrg_ctx* ctx, const int* chis, const double* T);
 
 /* Use `stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
@@ -112,15 +119,48 @@ int hotrg_set_fp64_threshold(hotrg_ctx* ctx, double flops);
  * 60 % of the free device memory.  Default 160e9. */
 int hotrg_set_slice_budget(hotrg_ctx* ctx, double bytes);
 
+/* Z2 (spin-flip) block form of the new-tensor contraction; enable = 1 is the
+ * default.  It applies while the leg parities are known: from
+ * hotrg_init_ising at h = 0, or declared by hotrg_set_parity.  The Ising
+ * tensor at h = 0 vanishes on odd total parity; every isometry column then
+ * has a definite parity (checked each step on the host: a column whose
+ * nonzero rows mix parities ends the block form for the rest of the run),
+ * and the bottleneck of Eq. (BottleneckPart) reduces to two dense blocks per
+ * c'-slice, a quarter of the dense flops.  The paper contracts densely; the
+ * result is the same up to rounding (fewer terms of exact zeros summed; in
+ * FP64 the same bits).  With enable = 0 the contraction is dense and the
+ * parities are still tracked. */
+int hotrg_set_z2(hotrg_ctx* ctx, int enable);
+
+/* Declare the parity (0 or 1) of every index of the current tensor:
+ * `parity` holds chis[0] entries for axis 0, then chis[1] for axis 1, ...
+ * (the two legs of an axis share them).  Checked on the device: if an
+ * element of odd total parity is nonzero the call returns EINVAL and the
+ * parities stay unknown.  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
+int hotrg_set_parity(hotrg_ctx* ctx, const int* parity);
+
+/* Read the known leg parities back in the layout of hotrg_set_parity;
+ * *n = number of entries (sum of the bond dimensions).  Errors: EINVAL (cap
+ * < *n), ESTATE (parities unknown). */
+int hotrg_leg_parity(hotrg_ctx* ctx, int* parity, int cap, int* n);
+
+/* Floating-point operations of the last step's bottleneck (Eq.
+ * BottleneckPart): *dense = 2 R^2 P_new P chi_c of the dense contraction,
+ * *performed = those of the GEMMs actually launched (a quarter of that with
+ * the Z2 block form, padding excluded); *z2_blocks = 1 if the block form
+ * ran.  Errors: EINVAL, ESTATE (no step yet). */
+int hotrg_bottleneck_flops(hotrg_ctx* ctx, double* dense, double* performed, int* z2_blocks);
+
 /* Record CUDA events around the phases of every later step (enable = 1) or
  * stop (0).  hotrg_step_times() then returns, after synchronising, the
  * milliseconds of the last step per phase: [0] leg permutation, [1]
  * environment Grams and A assembly, [2] Jacobi, [3] choice/truncation,
  * [4] BF16 split of T, [5] prime-side chain, [6] bottleneck GEMM, [7]
  * non-prime chain, [8] trace / normalisation, [9] FP32 warm start of the
- * eigen-solver (included in [2]), [10] its FP32 sweeps (included in [9]);
- * *n = 11.  launches[k] = number
- * of kernels timed in phase k (the bottleneck: one per c'-slice).
+ * eigen-solver (included in [2]), [10] its FP32 sweeps (included in [9]),
+ * [11] gathers and scatters of the Z2 block form; *n = 12.  launches[k] =
+ * number of timed regions of phase k (the bottleneck: one GEMM launch per
+ * c'-slice and n'_1 sub-range, two with the Z2 block form).
  * *contraction_fp64 = 1 if the last step's contraction ran in FP64. */
 int hotrg_profile(hotrg_ctx* ctx, int enable);
 int hotrg_step_times(hotrg_ctx* ctx, double ms[16], int launches[16], int* n, int* contraction_fp64);

@@ -68,6 +68,10 @@ def load():
         "hotrg_gemm_nt": (I, [I, I, I, I, P, P, P]),
         "hotrg_set_fp64_threshold": (I, [P, D]),
         "hotrg_set_slice_budget": (I, [P, D]),
+        "hotrg_set_z2": (I, [P, I]),
+        "hotrg_set_parity": (I, [P, ctypes.POINTER(I)]),
+        "hotrg_leg_parity": (I, [P, ctypes.POINTER(I), I, ctypes.POINTER(I)]),
+        "hotrg_bottleneck_flops": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
         "hotrg_profile": (I, [P, I]),
         "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -213,12 +217,42 @@ def hotrg_set_slice_budget(ctx, nbytes: float):
     _check(load().hotrg_set_slice_budget(ctx, float(nbytes)), "hotrg_set_slice_budget")
 
 
+def hotrg_set_z2(ctx, enable: bool):
+    _check(load().hotrg_set_z2(ctx, 1 if enable else 0), "hotrg_set_z2")
+
+
+def hotrg_set_parity(ctx, parity):
+    """Declare the parities of every index (axis 0's indices first, then axis 1, ...)."""
+    arr = (ctypes.c_int * len(parity))(*[int(x) for x in parity])
+    _check(load().hotrg_set_parity(ctx, arr), "hotrg_set_parity")
+
+
+def hotrg_leg_parity(ctx):
+    """Known parities of every index, or None while they are unknown."""
+    lib = load()
+    n = ctypes.c_int()
+    buf = (ctypes.c_int * 160)()
+    st = lib.hotrg_leg_parity(ctx, buf, 160, ctypes.byref(n))
+    if st == -7:
+        return None
+    _check(st, "hotrg_leg_parity")
+    return [buf[i] for i in range(n.value)]
+
+
+def hotrg_bottleneck_flops(ctx):
+    """(dense flops, performed flops, Z2 block form used) of the last step's bottleneck."""
+    dense, done, z2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().hotrg_bottleneck_flops(ctx, ctypes.byref(dense), ctypes.byref(done), ctypes.byref(z2)),
+           "hotrg_bottleneck_flops")
+    return dense.value, done.value, bool(z2.value)
+
+
 def hotrg_profile(ctx, enable: bool):
     _check(load().hotrg_profile(ctx, 1 if enable else 0), "hotrg_profile")
 
 
 PHASES = ["permute", "environment", "jacobi", "select", "split", "prime_chain", "bottleneck",
-          "nonprime_chain", "trace_norm", "jacobi_warm_start", "jacobi_fp32"]
+          "nonprime_chain", "trace_norm", "jacobi_warm_start", "jacobi_fp32", "z2_gather_scatter"]
 
 
 def hotrg_step_times(ctx):
@@ -254,7 +288,8 @@ class Hotrg:
     """Owning handle around one context, with torch streams and memory."""
 
     def __init__(self, d: int, beta: float, h: float = 0.0, precision: int = PREC_BF16X6,
-                 use_torch: bool = True, tensor=None, chis=None, fp64_below: float | None = None):
+                 use_torch: bool = True, tensor=None, chis=None, fp64_below: float | None = None,
+                 z2: bool = True):
         self.d = d
         self.beta = beta
         if tensor is None:
@@ -267,6 +302,7 @@ class Hotrg:
         hotrg_set_precision(self.ctx, precision)
         if fp64_below is not None:
             hotrg_set_fp64_threshold(self.ctx, fp64_below)
+        hotrg_set_z2(self.ctx, z2)
 
     def use_torch(self):
         import torch

@@ -160,7 +160,15 @@ struct hotrg_ctx {
   int last_leg_nnew[kMaxD - 1] = {0, 0, 0};
   long long last_lam_off[kMaxD - 1] = {0, 0, 0};
   long long last_u_off[kMaxD - 1] = {0, 0, 0};
+  // Z2 block structure: the parity of every index of every axis (both legs of an
+  // axis share it), known while z2_valid; used for the contraction while z2_enabled
+  int z2_enabled = 1;
+  int z2_valid = 0;
+  std::vector<unsigned char> par[kMaxD];
+  int last_z2 = 0;
+  double last_bn_dense = 0.0, last_bn_done = 0.0;
   // buffers
+  Buf Za, Zb, Zc, Zmap;   // Z2 blocks of the contraction operands, index maps
   Buf T, T2, Xp, parts, S, Amat, W, V, lam, U64, U32, legres, Y, state, counters, sweeps;
   Buf Ap, Bp, Cb, chA, chB;
   Buf J32, Gns, Vtmp;   // eigen-solver warm start
@@ -416,7 +424,10 @@ int hotrg_init_ising(int d, double beta, double h, hotrg_ctx** out) {
   for (int k = 0; k < d; ++k) {
     c->chis[k] = 2;
     c->order[k] = k;
+    c->par[k] = {0, 1};   // index 0 carries sqrt(cosh), index 1 sigma sqrt(sinh): even, odd
   }
+  // at h = 0 every element of odd total parity vanishes (spin-flip symmetry)
+  c->z2_valid = h == 0.0 ? 1 : 0;
   int r = dev_alloc(c, c->T, sizeof(double) << (2 * d));
   if (r == HOTRG_OK) {
     launch_init_ising((double*)c->T.p, d, beta, h, c->stream);
@@ -477,6 +488,7 @@ int hotrg_set_tensor(hotrg_ctx* c, const int* chis, const double* T) {
     return cuda_status(c);
   interchange_to_slots(c, (const double*)c->Xp.p, (double*)c->T.p);
   c->last_valid = 0;
+  c->z2_valid = 0;   // until hotrg_set_parity declares and checks the parities
   int r = cuda_status(c);
   if (r != HOTRG_OK) return r;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
@@ -506,7 +518,7 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
@@ -753,6 +765,46 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                   (int*)c->sweeps.p + (mat_of_leg[j] - grp_first_mat[grp_of[j]]), s);
   }
 
+  // ---- Z2 blocks at zero field: the parity of each new index is that of the rows
+  // its column of U occupies (every nonzero row of a column must agree; a column
+  // that mixes parities ends the block treatment for the rest of the run)
+  // (parities are tracked while known, and used when the block form is enabled)
+  bool z2 = false, track = false;
+  std::vector<unsigned char> newpar[kMaxD];
+  if (c->z2_valid) {
+    std::vector<double> hu((size_t)u_total);
+    if (cudaMemcpyAsync(hu.data(), c->U64.p, sizeof(double) * u_total, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    bool pure = true;
+    for (int j = 1; j < d && pure; ++j) {
+      const std::vector<unsigned char>& pj = c->par[to[j]];
+      const int chj = chij[j], n = chj * chj;
+      if ((int)pj.size() != chj) {
+        pure = false;
+        break;
+      }
+      newpar[j].assign(nnew[j], 0);
+      for (int col = 0; col < nnew[j]; ++col) {
+        int seen = -1;
+        for (int r = 0; r < n; ++r) {
+          if (hu[u_off[j] + (long long)r * nnew[j] + col] == 0.0) continue;
+          const int pr = pj[r % chj] ^ pj[r / chj];
+          if (seen < 0) seen = pr;
+          else if (seen != pr) pure = false;
+        }
+        newpar[j][col] = (unsigned char)(seen < 0 ? 0 : seen);
+      }
+    }
+    if (pure) {
+      track = true;
+      z2 = c->z2_enabled != 0;
+    } else {
+      c->z2_valid = 0;
+    }
+  }
+
   // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
   const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
   const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
@@ -779,12 +831,15 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const int nnew1 = nnew[1];
   int n1_chunk = nnew1;
   {
+    // the Z2 blocks of B and C hold about half of B and C again
     const double per_unit =
-        (double)(Ns / nnew1) * ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
+        (z2 ? 1.6 : 1.0) * (double)(Ns / nnew1) *
+            ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
         2.0 * (double)elt * (double)chain_max / nnew1;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    double budget = std::min(0.6 * (double)free_b + (double)(c->Bp.bytes + c->Cb.bytes + c->chA.bytes + c->chB.bytes),
+    double budget = std::min(0.6 * (double)free_b + (double)(c->Bp.bytes + c->Cb.bytes + c->chA.bytes +
+                                                             c->chB.bytes + c->Zb.bytes + c->Zc.bytes),
                              c->slice_budget_bytes);
     n1_chunk = (int)std::max(1.0, std::min((double)nnew1, std::floor(budget / per_unit)));
   }
@@ -792,20 +847,126 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const long long chain_sub = (chain_max / nnew1) * n1_chunk;
   CHECK_ALLOC(dev_alloc(c, c->chA, elt * chain_sub));
   CHECK_ALLOC(dev_alloc(c, c->chB, elt * chain_sub));
+  // Z2 index maps.  Rows of T and the contracted index (rho, n^') run over the same
+  // slots with the same parities, so one list per parity b serves as the row map
+  // (first R_b entries) and, padded with -1 to Kp_b, as the K map of block b.
+  long long Rb[2] = {0, 0}, Kpb[2] = {0, 0}, maxL = 0;
+  long long moff_rowblk = 0, moff_rowpos = 0, moff_k[2] = {0, 0};
+  struct Z2Chunk {
+    long long off_blk, off_pos, off_list[2], L[2];
+  };
+  std::vector<Z2Chunk> zch;
+  if (z2) {
+    std::vector<int> hmap;
+    auto push = [&](const std::vector<int>& v) {
+      long long off = (long long)hmap.size();
+      hmap.insert(hmap.end(), v.begin(), v.end());
+      while (hmap.size() % 4) hmap.push_back(0);
+      return off;
+    };
+    std::vector<int> rowblk(R), rowpos(R), kmap[2];
+    for (long long r = 0; r < R; ++r) {
+      long long idx = r;
+      int p_ = 0;
+      for (int k = d - 1; k >= 0; --k) {
+        const int sz = c->chis[to[k]];
+        p_ ^= c->par[to[k]][idx % sz];
+        idx /= sz;
+      }
+      rowblk[r] = p_;
+      rowpos[r] = (int)kmap[p_].size();
+      kmap[p_].push_back((int)r);
+    }
+    for (int b = 0; b < 2; ++b) {
+      Rb[b] = (long long)kmap[b].size();
+      Kpb[b] = fp64 ? Rb[b] : (Rb[b] + 63) / 64 * 64;
+      kmap[b].resize(Kpb[b], -1);
+    }
+    moff_rowblk = push(rowblk);
+    moff_rowpos = push(rowpos);
+    for (int b = 0; b < 2; ++b) moff_k[b] = push(kmap[b]);
+    // parity of a bottleneck column (n', n~): new legs from U, old legs as before
+    std::vector<unsigned char> pnp((size_t)Pn), ptl((size_t)P);
+    for (long long x = 0; x < Pn; ++x) {
+      long long idx = x;
+      int p_ = 0;
+      for (int k = d - 1; k >= 1; --k) {
+        p_ ^= newpar[k][idx % nnew[k]];
+        idx /= nnew[k];
+      }
+      pnp[x] = (unsigned char)p_;
+    }
+    for (long long x = 0; x < P; ++x) {
+      long long idx = x;
+      int p_ = 0;
+      for (int k = d - 1; k >= 1; --k) {
+        p_ ^= c->par[to[k]][idx % chij[k]];
+        idx /= chij[k];
+      }
+      ptl[x] = (unsigned char)p_;
+    }
+    const long long per_n1 = Ns / nnew1;
+    for (int n1lo = 0; n1lo < nnew1; n1lo += n1_chunk) {
+      const long long Nc = (long long)std::min(n1_chunk, nnew1 - n1lo) * per_n1;
+      const long long base = (long long)n1lo * per_n1;
+      std::vector<int> colblk(Nc), colpos(Nc), lst[2];
+      for (long long n = 0; n < Nc; ++n) {
+        const long long g = base + n;
+        const int p_ = pnp[g / P] ^ ptl[g % P];
+        colblk[n] = p_;
+        colpos[n] = (int)lst[p_].size();
+        lst[p_].push_back((int)n);
+      }
+      Z2Chunk ch;
+      ch.off_blk = push(colblk);
+      ch.off_pos = push(colpos);
+      for (int b = 0; b < 2; ++b) {
+        ch.off_list[b] = push(lst[b]);
+        ch.L[b] = (long long)lst[b].size();
+        maxL = std::max(maxL, ch.L[b]);
+      }
+      zch.push_back(ch);
+    }
+    CHECK_ALLOC(dev_alloc(c, c->Zmap, sizeof(int) * hmap.size()));
+    if (cudaMemcpyAsync(c->Zmap.p, hmap.data(), sizeof(int) * hmap.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+  }
+  const int* zmap = (const int*)c->Zmap.p;
+  const long long ldz = (maxL + 3) / 4 * 4;   // row pitch of the C blocks
   if (fp64) {
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Nsub * R));
     CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(double) * R * Nsub));
+    if (z2) {
+      CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(double) * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Zb, sizeof(double) * maxL * (Kpb[0] + Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Zc, sizeof(double) * R * ldz));
+      double* za = (double*)c->Za.p;
+      launch_z2_gather_f64(Tc, R, zmap + moff_k[0], (int)Rb[0], zmap + moff_k[0], (int)Kpb[0], za, s);
+      launch_z2_gather_f64(Tc, R, zmap + moff_k[1], (int)Rb[1], zmap + moff_k[1], (int)Kpb[1],
+                           za + Rb[0] * Kpb[0], s);
+    }
   } else {
-    CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
     CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
-    if (Kpad != R) {
-      cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
-      cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
-    }
+    if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
     Phase ph(c, 4);
-    launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
+    if (z2) {
+      CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(__nv_bfloat16) * npieces * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Zb, sizeof(__nv_bfloat16) * npieces * maxL * (Kpb[0] + Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Zc, sizeof(float) * R * ldz));
+      __nv_bfloat16* za = (__nv_bfloat16*)c->Za.p;
+      launch_z2_gather_split(Tc, R, zmap + moff_k[0], (int)Rb[0], zmap + moff_k[0], (int)Kpb[0], za,
+                             Rb[0] * Kpb[0], npieces, s);
+      launch_z2_gather_split(Tc, R, zmap + moff_k[1], (int)Rb[1], zmap + moff_k[1], (int)Kpb[1],
+                             za + npieces * Rb[0] * Kpb[0], Rb[1] * Kpb[1], npieces, s);
+    } else {
+      CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
+      launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
+    }
   }
+  double bn_done = 0.0;
   CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
   double* Tn = (double*)c->T2.p;
 
@@ -891,7 +1052,60 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       in = out;
     }
     // -- bottleneck, Eq. (BottleneckPart): C[(c, n^)][(n', n~)] = T . B^T
-    {
+    if (z2) {
+      // blocks b = 0, 1: rows and K of parity b, columns of parity b ^ q
+      const int q = c->par[to[0]][sl];
+      const Z2Chunk& ch = zch[n1lo / n1_chunk];
+      const void* cblk[2] = {nullptr, nullptr};
+      long long ldb_[2] = {1, 1};
+      for (int b = 0; b < 2; ++b) {
+        const long long Nb = ch.L[b ^ q];
+        if (Rb[b] == 0 || Nb == 0) continue;
+        const int* nmap = zmap + ch.off_list[b ^ q];
+        const int* kmap = zmap + moff_k[b];
+        const long long a_off = b == 0 ? 0 : Rb[0] * Kpb[0];
+        const long long b_off = b == 0 ? 0 : maxL * Kpb[0];
+        const long long c_off = b == 0 ? 0 : Rb[0] * ldz;
+        if (fp64) {
+          double* zb = (double*)c->Zb.p + b_off;
+          double* zc = (double*)c->Zc.p + c_off;
+          {
+            Phase pg(c, 11);
+            launch_z2_gather_f64((const double*)c->Bp.p, R, nmap, (int)Nb, kmap, (int)Kpb[b], zb, s);
+          }
+          Phase ph(c, 6);
+          launch_gemm_nt_f64((const double*)c->Za.p + a_off, Kpb[b], zb, Kpb[b], zc, ldz, 0, (int)Rb[b],
+                             (int)Nb, Kpb[b], 1, 0, s);
+          cblk[b] = zc;
+        } else {
+          __nv_bfloat16* zb = (__nv_bfloat16*)c->Zb.p + npieces * b_off;
+          float* zc = (float*)c->Zc.p + c_off;
+          {
+            Phase pg(c, 11);
+            launch_z2_gather_bf16((const __nv_bfloat16*)c->Bp.p, Kpad, Nc * Kpad, nmap, (int)Nb, kmap,
+                                  (int)Kpb[b], zb, Nb * Kpb[b], npieces, s);
+          }
+          Phase ph(c, 6);
+          if (launch_tc_gemm((const __nv_bfloat16*)c->Za.p + npieces * a_off, (int)Rb[b], zb, (int)Nb,
+                             (int)Kpb[b], npieces, nterms, terms_a, terms_b, zc, ldz,
+                             &((DevState*)c->state.p)->status, s, nullptr) != 0)
+            return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+          cblk[b] = zc;
+        }
+        ldb_[b] = ldz;
+        bn_done += 2.0 * (double)Rb[b] * (double)Nb * (double)Rb[b];
+      }
+      Phase pg(c, 11);
+      if (fp64)
+        launch_z2_scatter_f64((const double*)cblk[0], ldb_[0], (const double*)cblk[1], ldb_[1],
+                              zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk, zmap + ch.off_pos,
+                              q, (int)R, (int)Nc, (double*)c->Cb.p, s);
+      else
+        launch_z2_scatter_f32((const float*)cblk[0], ldb_[0], (const float*)cblk[1], ldb_[1],
+                              zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk, zmap + ch.off_pos,
+                              q, (int)R, (int)Nc, (float*)c->Cb.p, s);
+    } else {
+    bn_done += 2.0 * (double)R * (double)Nc * (double)R;
     Phase ph(c, 6);
     if (fp64) {
       launch_gemm_nt_f64(Tc, R, (const double*)c->Bp.p, R, (double*)c->Cb.p, Nc, 0, (int)R, (int)Nc,
@@ -948,6 +1162,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
 
   // ---- bond dims of the new tensor (Sec. 4.2.15 with the axes kept physical)
   for (int j = 1; j < d; ++j) c->chis[to[j]] = nnew[j];
+  if (track)
+    for (int j = 1; j < d; ++j) c->par[to[j]] = newpar[j];
+  c->last_z2 = z2 ? 1 : 0;
+  c->last_bn_dense = bn_flops;
+  c->last_bn_done = bn_done;
   c->p += 1;
   // ---- trace, Y, ratio X, ln Z, normalisation (Secs. 4.2.11-4.2.16)
   CHECK_ALLOC(dev_alloc(c, c->T, sizeof(double) * Rn * Rn));
@@ -1145,6 +1364,70 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
   return status;
 }
 
+int hotrg_set_z2(hotrg_ctx* c, int enable) {
+  if (!c) return HOTRG_EINVAL;
+  c->z2_enabled = enable ? 1 : 0;
+  return HOTRG_OK;
+}
+
+int hotrg_set_parity(hotrg_ctx* c, const int* parity) {
+  if (!c || !parity) return HOTRG_EINVAL;
+  if (c->poisoned) return HOTRG_ESTATE;
+  const int d = c->d;
+  std::vector<unsigned char> par[kMaxD];
+  int off = 0;
+  for (int k = 0; k < d; ++k) {
+    for (int v = 0; v < c->chis[k]; ++v) {
+      const int x = parity[off + v];
+      if (x != 0 && x != 1) return HOTRG_EINVAL;
+      par[k].push_back((unsigned char)x);
+    }
+    off += c->chis[k];
+  }
+  Z2Slots sl;
+  sl.d = d;
+  for (int k = 0; k < d; ++k) {
+    const int ax = c->order[k];
+    sl.chi[k] = c->chis[ax];
+    sl.mask[k] = 0;
+    for (int v = 0; v < c->chis[ax]; ++v) sl.mask[k] |= (unsigned)par[ax][v] << v;
+  }
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (3 * 2 * kMaxD + 3)));
+  int* cnt = (int*)c->counters.p;
+  int bad = 0;
+  cudaMemsetAsync(cnt, 0, sizeof(int), c->stream);
+  launch_z2_check((const double*)c->T.p, sl, tensor_elems(c), cnt, c->stream);
+  if (cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_status(c);
+  if (bad) return HOTRG_EINVAL;
+  for (int k = 0; k < d; ++k) c->par[k] = par[k];
+  c->z2_valid = 1;
+  return HOTRG_OK;
+}
+
+int hotrg_leg_parity(hotrg_ctx* c, int* parity, int cap, int* n_out) {
+  if (!c || !parity) return HOTRG_EINVAL;
+  if (!c->z2_valid) return HOTRG_ESTATE;
+  int n = 0;
+  for (int k = 0; k < c->d; ++k) n += c->chis[k];
+  if (n_out) *n_out = n;
+  if (cap < n) return HOTRG_EINVAL;
+  int off = 0;
+  for (int k = 0; k < c->d; ++k)
+    for (int v = 0; v < c->chis[k]; ++v) parity[off++] = c->par[k][v];
+  return HOTRG_OK;
+}
+
+int hotrg_bottleneck_flops(hotrg_ctx* c, double* dense, double* performed, int* z2_blocks) {
+  if (!c) return HOTRG_EINVAL;
+  if (!c->last_valid) return HOTRG_ESTATE;
+  if (dense) *dense = c->last_bn_dense;
+  if (performed) *performed = c->last_bn_done;
+  if (z2_blocks) *z2_blocks = c->last_z2;
+  return HOTRG_OK;
+}
+
 int hotrg_set_fp64_threshold(hotrg_ctx* c, double flops) {
   if (!c || !(flops >= 0.0)) return HOTRG_EINVAL;
   c->fp64_below = flops;
@@ -1177,7 +1460,7 @@ int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int*
     ms[m.first] += t;
     if (launches) launches[m.first] += 1;
   }
-  if (n) *n = 11;
+  if (n) *n = 12;
   if (contraction_fp64) *contraction_fp64 = c->last_fp64;
   return HOTRG_OK;
 }
@@ -1201,7 +1484,7 @@ void hotrg_free(hotrg_ctx* c) {
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
   delete c;

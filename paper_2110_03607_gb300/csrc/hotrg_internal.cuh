@@ -100,6 +100,29 @@ void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, cons
                          void* out, int out_mode, cudaStream_t s);
 enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2 };
 
+// ---- kernels_z2.cu
+struct Z2Slots {
+  int d;
+  int chi[kMaxD];
+  unsigned mask[kMaxD];   // bit v: parity of index v of the slot
+};
+void launch_z2_check(const double* T, const Z2Slots& sl, long long total, int* count, cudaStream_t s);
+void launch_z2_gather_split(const double* src, long long ld, const int* rowmap, int nrows,
+                            const int* colmap, int ncols, __nv_bfloat16* dst, long long piece_stride,
+                            int npieces, cudaStream_t s);
+void launch_z2_gather_f64(const double* src, long long ld, const int* rowmap, int nrows,
+                          const int* colmap, int ncols, double* dst, cudaStream_t s);
+void launch_z2_gather_bf16(const __nv_bfloat16* src, long long ld, long long src_piece_stride,
+                           const int* rowmap, int nrows, const int* colmap, int ncols,
+                           __nv_bfloat16* dst, long long dst_piece_stride, int npieces,
+                           cudaStream_t s);
+void launch_z2_scatter_f32(const float* c0, long long ld0, const float* c1, long long ld1,
+                           const int* rowblk, const int* rowpos, const int* colblk, const int* colpos,
+                           int q, int nrows, int ncols, float* dense, cudaStream_t s);
+void launch_z2_scatter_f64(const double* c0, long long ld0, const double* c1, long long ld1,
+                           const int* rowblk, const int* rowpos, const int* colblk, const int* colpos,
+                           int q, int nrows, int ncols, double* dense, cudaStream_t s);
+
 // ---- kernels_tc_gemm.cu
 // C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,

@@ -169,10 +169,11 @@ def _golden(name):
     return out
 
 
-def test_ising3d_chi16_free_energy_matches_oracle_reference(pkg):
+@pytest.mark.parametrize("z2", [True, False])
+def test_ising3d_chi16_free_energy_matches_oracle_reference(pkg, z2):
     gold = _golden("ising3d_chi16")
     assert len(gold) >= 5
-    g = pkg.Hotrg(3, 0.2216544, 0.0, precision=pkg.PREC_BF16X6)
+    g = pkg.Hotrg(3, 0.2216544, 0.0, precision=pkg.PREC_BF16X6, z2=z2)
     try:
         for step in range(1, max(gold) + 1):
             g.step((2 + step - 1) % 3, 16)
