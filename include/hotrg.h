@@ -126,10 +126,11 @@ int hotrg_set_slice_budget(hotrg_ctx* ctx, double bytes);
  * has a definite parity (checked each step on the host: a column whose
  * nonzero rows mix parities ends the block form for the rest of the run),
  * and the bottleneck of Eq. (BottleneckPart) reduces to two dense blocks per
- * c'-slice, a quarter of the dense flops.  The paper contracts densely; the
- * result is the same up to rounding (fewer terms of exact zeros summed; in
- * FP64 the same bits).  With enable = 0 the contraction is dense and the
- * parities are still tracked. */
+ * c'-slice, a quarter of the dense flops; the environment Grams (Sec. 3.2)
+ * are block diagonal in the same way and are computed as two blocks.  The
+ * paper works densely; the result is the same up to rounding (products with
+ * an exact-zero factor are dropped, partial sums grouped differently).  With
+ * enable = 0 everything is dense and the parities are still tracked. */
 int hotrg_set_z2(hotrg_ctx* ctx, int enable);
 
 /* Declare the parity (0 or 1) of every index of the current tensor:

@@ -167,8 +167,15 @@ struct hotrg_ctx {
   std::vector<unsigned char> par[kMaxD];
   int last_z2 = 0;
   double last_bn_dense = 0.0, last_bn_done = 0.0;
+  // pinned host staging for index maps, reused once the copy recorded in hpin_ev is done
+  void* hpin = nullptr;
+  size_t hpin_bytes = 0;
+  cudaEvent_t hpin_ev = nullptr;
+  int hpin_pending = 0;
   // buffers
   Buf Za, Zb, Zc, Zmap;   // Z2 blocks of the contraction operands, index maps
+  Buf Zg;                 // Z2 index maps of the environment Grams and the eigen blocks
+  Buf Eb;                 // Z2 blocks of A, W, V for the eigen-solver
   Buf T, T2, Xp, parts, S, Amat, W, V, lam, U64, U32, legres, Y, state, counters, sweeps;
   Buf Ap, Bp, Cb, chA, chB;
   Buf J32, Gns, Vtmp;   // eigen-solver warm start
@@ -248,6 +255,35 @@ struct Phase {
       return _r;                       \
     }                                  \
   } while (0)
+
+// Pinned host buffer of at least `bytes` for an index-map upload; waits for the
+// previous upload from it to finish.  nullptr if pinned memory is not available.
+void* pinned_stage(hotrg_ctx* c, size_t bytes) {
+  if (c->hpin_pending) {
+    cudaEventSynchronize(c->hpin_ev);
+    c->hpin_pending = 0;
+  }
+  if (!c->hpin_ev && cudaEventCreateWithFlags(&c->hpin_ev, cudaEventDisableTiming) != cudaSuccess) {
+    c->hpin_ev = nullptr;
+    return nullptr;
+  }
+  if (c->hpin_bytes < bytes) {
+    if (c->hpin) cudaFreeHost(c->hpin);
+    c->hpin = nullptr;
+    c->hpin_bytes = 0;
+    if (cudaMallocHost(&c->hpin, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->hpin = nullptr;
+      return nullptr;
+    }
+    c->hpin_bytes = bytes;
+  }
+  return c->hpin;
+}
+
+// Jacobi grid-barrier counters: 3 per matrix of one launch (up to 4 (d - 1) parity
+// blocks), then 3 for the FP32 warm start
+constexpr int kCounters32 = 3 * 4 * kMaxD;
 
 int num_sms() {
   static int n = 0;
@@ -518,7 +554,7 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
@@ -651,28 +687,178 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   CHECK_ALLOC(dev_alloc(c, c->J32, sizeof(float) * 2 * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Gns, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Vtmp, sizeof(double) * total_mat_elems));
-  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (3 * 2 * kMaxD + 3)));
-  CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 2 * kMaxD));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (kCounters32 + 3)));
+  CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 6 * kMaxD));
 
+  // Gram of leg j, kind: X = T with the free pair (n_j or n'_j, c' or c) first, rest after
+  // kind 0: S^  free (n_j, c');  1: S~  free (n_j, c);
+  // kind 2: S^' free (n'_j, c'); 3: S~' free (n'_j, c)
+  auto gram_dims = [&](int j, int kind, long long* size, long long* ist, int* pslot) {
+    const int fpos = (kind < 2) ? j : d + j;
+    const int cpos = (kind == 0 || kind == 2) ? d : 0;
+    int nd = 0;
+    size[nd] = chij[j];
+    pslot[nd] = j;
+    ist[nd++] = fpos < d ? rs[fpos] : cs[fpos - d];
+    size[nd] = chi_c;
+    pslot[nd] = 0;
+    ist[nd++] = cpos < d ? rs[cpos] : cs[cpos - d];
+    for (int q = 0; q < 2 * d; ++q) {
+      if (q == fpos || q == cpos) continue;
+      size[nd] = q < d ? c->chis[to[q]] : c->chis[to[q - d]];
+      pslot[nd] = q % d;
+      ist[nd++] = q < d ? rs[q] : cs[q - d];
+    }
+    return nd;
+  };
+  // Z2 blocks of the Grams: the rows (free pair) and the summed index, both listed even
+  // parity first, as element offsets into T; per leg the block and position of each row
+  const bool z2g = c->z2_valid && c->z2_enabled;
+  long long gz_roff[kMaxD][4], gz_koff[kMaxD][4], gz_rowmap[kMaxD];
+  long long gz_mb[kMaxD][2], gz_Kb[kMaxD][4][2], gz_n64 = 0, gz_eig[kMaxD];
+  int eig_nb[kMaxD][2];
+  if (z2g) {
+    long long n64 = 0, n32 = 0;
+    for (int j = 1; j < d; ++j) {
+      const long long m = (long long)chij[j] * chi_c;
+      for (int kind = 0; kind < 4; ++kind) {
+        gz_roff[j][kind] = n64;
+        gz_koff[j][kind] = n64 + m;
+        n64 += m + RR / m;
+      }
+      gz_rowmap[j] = n32;
+      n32 += 2 * m;
+      gz_eig[j] = n32;                       // rows by parity, block, position (n = chi_j^2)
+      n32 += 3LL * chij[j] * chij[j];
+    }
+    gz_n64 = n64;   // the int maps follow the offsets
+    const size_t bytes = sizeof(long long) * n64 + sizeof(int) * n32;
+    long long* h64 = (long long*)pinned_stage(c, bytes);
+    std::vector<long long> h64v;
+    if (!h64) {
+      h64v.resize((bytes + 7) / 8);
+      h64 = h64v.data();
+    }
+    int* h32 = (int*)(h64 + n64);
+    std::vector<long long> offs;
+    std::vector<unsigned char> pk;
+    for (int j = 1; j < d; ++j) {
+      const std::vector<unsigned char>& pf = c->par[to[j]];
+      const std::vector<unsigned char>& pc = c->par[to[0]];
+      int* blk = h32 + gz_rowmap[j];
+      int* pos = blk + (long long)chij[j] * chi_c;
+      long long cnt[2] = {0, 0};
+      for (int f = 0; f < chij[j]; ++f)
+        for (int cu = 0; cu < chi_c; ++cu) {
+          const int b = pf[f] ^ pc[cu];
+          blk[f * chi_c + cu] = b;
+          pos[f * chi_c + cu] = (int)cnt[b]++;
+        }
+      gz_mb[j][0] = cnt[0];
+      gz_mb[j][1] = cnt[1];
+      {
+        // composite index r = hat + check chi_j of A^(j): parity pf[hat] ^ pf[check]
+        const int cj = chij[j], n = cj * cj;
+        int* rows = h32 + gz_eig[j];
+        int* eb = rows + n;
+        int* ep = eb + n;
+        int ec[2] = {0, 0};
+        for (int r = 0; r < n; ++r) {
+          const int b = pf[r % cj] ^ pf[r / cj];
+          eb[r] = b;
+          ep[r] = ec[b]++;
+        }
+        int w2[2] = {0, ec[0]};
+        for (int r = 0; r < n; ++r) rows[w2[eb[r]]++] = r;
+        eig_nb[j][0] = ec[0];
+        eig_nb[j][1] = ec[1];
+      }
+      for (int kind = 0; kind < 4; ++kind) {
+        long long size[kMaxDims], ist[kMaxDims];
+        int pslot[kMaxDims];
+        const int nd = gram_dims(j, kind, size, ist, pslot);
+        long long* ro = h64 + gz_roff[j][kind];
+        long long w[2] = {0, cnt[0]};
+        for (int f = 0; f < chij[j]; ++f)
+          for (int cu = 0; cu < chi_c; ++cu) ro[w[pf[f] ^ pc[cu]]++] = f * ist[0] + cu * ist[1];
+        // the summed index, row-major over dims 2 .. nd-1, by an odometer
+        const long long K = RR / ((long long)chij[j] * chi_c);
+        offs.resize(K);
+        pk.resize(K);
+        long long idx[kMaxDims] = {0};
+        long long off = 0;
+        int par_ = 0;
+        for (int q = 2; q < nd; ++q) par_ ^= c->par[to[pslot[q]]][0];
+        long long kc[2] = {0, 0};
+        for (long long k = 0; k < K; ++k) {
+          offs[k] = off;
+          pk[k] = (unsigned char)par_;
+          ++kc[par_];
+          for (int q = nd - 1; q >= 2; --q) {
+            const std::vector<unsigned char>& pq = c->par[to[pslot[q]]];
+            par_ ^= pq[idx[q]];
+            off -= idx[q] * ist[q];
+            if (++idx[q] < size[q]) {
+              par_ ^= pq[idx[q]];
+              off += idx[q] * ist[q];
+              break;
+            }
+            idx[q] = 0;
+            par_ ^= pq[0];
+          }
+        }
+        long long* ko = h64 + gz_koff[j][kind];
+        long long wk[2] = {0, kc[0]};
+        for (long long k = 0; k < K; ++k) ko[wk[pk[k]]++] = offs[k];
+        gz_Kb[j][kind][0] = kc[0];
+        gz_Kb[j][kind][1] = kc[1];
+      }
+    }
+    CHECK_ALLOC(dev_alloc(c, c->Zg, bytes));
+    if (cudaMemcpyAsync(c->Zg.p, h64, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    if (h64v.empty()) {
+      cudaEventRecord(c->hpin_ev, s);
+      c->hpin_pending = 1;
+    }
+  }
   for (int j = 1; j < d; ++j) {
     Phase ph(c, 1);
     const long long m = (long long)chij[j] * chi_c;
     const long long K = RR / m;
     for (int kind = 0; kind < 4; ++kind) {
-      // kind 0: S^  free (n_j, c');  1: S~  free (n_j, c);
-      // kind 2: S^' free (n'_j, c'); 3: S~' free (n'_j, c)
-      const int fpos = (kind < 2) ? j : d + j;
-      const int cpos = (kind == 0 || kind == 2) ? d : 0;
       long long size[kMaxDims], ist[kMaxDims];
-      int nd = 0;
-      size[nd] = chij[j];
-      ist[nd++] = fpos < d ? rs[fpos] : cs[fpos - d];
-      size[nd] = chi_c;
-      ist[nd++] = cpos < d ? rs[cpos] : cs[cpos - d];
-      for (int q = 0; q < 2 * d; ++q) {
-        if (q == fpos || q == cpos) continue;
-        size[nd] = q < d ? c->chis[to[q]] : c->chis[to[q - d]];
-        ist[nd++] = q < d ? rs[q] : cs[q - d];
+      int pslot[kMaxDims];
+      const int nd = gram_dims(j, kind, size, ist, pslot);
+      double* Sdst = (double*)c->S.p + ((long long)(j - 1) * 4 + kind) * mmax * mmax;
+      if (z2g) {
+        const long long* zg = (const long long*)c->Zg.p;
+        double* X = (double*)c->Xp.p;
+        launch_z2_gather_rc(Tc, zg + gz_roff[j][kind], (int)m, zg + gz_koff[j][kind], K, X, s);
+        const double* pb[2] = {(const double*)c->parts.p, (const double*)c->parts.p};
+        int nsb[2] = {0, 0};
+        long long poff = 0;
+        for (int b = 0; b < 2; ++b) {
+          const long long mb = gz_mb[j][b], Kb = gz_Kb[j][kind][b];
+          if (mb == 0 || Kb == 0) continue;
+          const long long r0 = b == 0 ? 0 : gz_mb[j][0], k0 = b == 0 ? 0 : gz_Kb[j][kind][0];
+          const int tiles = (int)((mb + 63) / 64);
+          const int upper_tiles = tiles * (tiles + 1) / 2;
+          int nsplit = std::max(1, std::min<int>(nsplit_max, (4 * num_sms()) / upper_tiles));
+          nsplit = (int)std::min<long long>(nsplit, std::max<long long>(1, Kb / 64));
+          double* pdst = (double*)c->parts.p + poff;
+          launch_gemm_nt_f64(X + r0 * K + k0, K, X + r0 * K + k0, K, pdst, mb, mb * mb, (int)mb, (int)mb,
+                             Kb, nsplit, 1, s);
+          long long kchunk = (Kb + nsplit - 1) / nsplit;
+          kchunk = (kchunk + 15) / 16 * 16;
+          nsb[b] = (int)((Kb + kchunk - 1) / kchunk);
+          pb[b] = pdst;
+          poff += (long long)nsb[b] * mb * mb;
+        }
+        const int* zi = (const int*)(zg + gz_n64) + gz_rowmap[j];
+        launch_z2_reduce_sym(pb[0], nsb[0], (int)gz_mb[j][0], pb[1], nsb[1], (int)gz_mb[j][1], zi,
+                             zi + m, (int)m, Sdst, s);
+        continue;
       }
       launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
       // fill every SM with the same number of CTAs: tiles x splits <= 4 per SM
@@ -686,7 +872,6 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       long long kchunk = (K + nsplit - 1) / nsplit;
       kchunk = (kchunk + 15) / 16 * 16;
       int used = (int)((K + kchunk - 1) / kchunk);
-      double* Sdst = (double*)c->S.p + ((long long)(j - 1) * 4 + kind) * mmax * mmax;
       launch_reduce_sym((const double*)c->parts.p, used, (int)m, Sdst, s);
     }
     double* S0 = (double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
@@ -695,21 +880,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                       (double*)c->Amat.p + mat_elem_off[2 * j + 1], s);
   }
 
-  // ---- eigen-decomposition (Sec. 4.2.5), batched per group
-  for (int g = 0; g < ngrp; ++g) {
-    Phase ph(c, 2);
-    int cnt = 0;
-    long long base = -1;
-    for (int j = 1; j < d; ++j)
-      if (grp_of[j] == g) {
-        cnt += 2;
-        if (base < 0 || mat_elem_off[2 * j] < base) base = mat_elem_off[2 * j];
-      }
-    const int n = grp_n[g];
+  // ---- eigen-decomposition (Sec. 4.2.5), batched over matrices of equal size
+  auto eig_batch = [&](const double* Ag, double* Wg, double* Vg, int n, int cnt, int* sweeps_out) -> int {
     const long long nn = (long long)n * n;
-    double* Wg = (double*)c->W.p + base;
-    double* Vg = (double*)c->V.p + base;
-    const double* Ag = (const double*)c->Amat.p + base;
     const double* Ainit = Ag;
     if (n >= 32) {
       Phase phw(c, 9);
@@ -722,7 +895,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       int ok32;
       {
         Phase ph32(c, 10);
-        ok32 = launch_jacobi32_block(Ag, W32, V32, n, cnt, 30, (int*)c->counters.p + 3 * 2 * kMaxD, s) == 0;
+        ok32 = launch_jacobi32_block(Ag, W32, V32, n, cnt, 30, (int*)c->counters.p + kCounters32, s) == 0;
         if (!ok32) cudaGetLastError();
       }
       if (ok32) {
@@ -737,9 +910,88 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         Ainit = nullptr;
       }
     }
-    if (launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p, (int*)c->sweeps.p,
-                      (DevState*)c->state.p, s) != 0)
-      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    return launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p, sweeps_out,
+                         (DevState*)c->state.p, s);
+  };
+  if (!z2g) {
+    for (int g = 0; g < ngrp; ++g) {
+      Phase ph(c, 2);
+      int cnt = 0;
+      long long base = -1;
+      for (int j = 1; j < d; ++j)
+        if (grp_of[j] == g) {
+          cnt += 2;
+          if (base < 0 || mat_elem_off[2 * j] < base) base = mat_elem_off[2 * j];
+        }
+      if (eig_batch((const double*)c->Amat.p + base, (double*)c->W.p + base, (double*)c->V.p + base,
+                    grp_n[g], cnt, (int*)c->sweeps.p + grp_first_mat[g]) != 0)
+        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    }
+  } else {
+    // A^(j), A'^(j) are block diagonal in the parity of (hat, check): gather the blocks,
+    // decompose each size group, scatter W and V back (zeros between parities)
+    Phase ph(c, 2);
+    const int* zi = (const int*)((const long long*)c->Zg.p + gz_n64);
+    long long boff[kMaxD][2][2];
+    int bidx[kMaxD][2][2];
+    std::vector<int> sizes;
+    for (int j = 1; j < d; ++j)
+      for (int b = 0; b < 2; ++b)
+        if (eig_nb[j][b] > 0 && std::find(sizes.begin(), sizes.end(), eig_nb[j][b]) == sizes.end())
+          sizes.push_back(eig_nb[j][b]);
+    long long eoff = 0;
+    int nblk = 0;
+    std::vector<std::pair<long long, int>> grp_first(sizes.size());   // element offset, block index
+    std::vector<int> grp_cnt(sizes.size(), 0);
+    for (size_t g = 0; g < sizes.size(); ++g) {
+      grp_first[g] = {eoff, nblk};
+      for (int j = 1; j < d; ++j)
+        for (int k = 0; k < 2; ++k)
+          for (int b = 0; b < 2; ++b)
+            if (eig_nb[j][b] == sizes[g]) {
+              boff[j][k][b] = eoff;
+              bidx[j][k][b] = nblk++;
+              eoff += (long long)sizes[g] * sizes[g];
+              ++grp_cnt[g];
+            }
+    }
+    CHECK_ALLOC(dev_alloc(c, c->Eb, sizeof(double) * 3 * std::max<long long>(eoff, 1)));
+    double* Ab = (double*)c->Eb.p;
+    double* Wb = Ab + eoff;
+    double* Vb = Wb + eoff;
+    for (int j = 1; j < d; ++j)
+      for (int k = 0; k < 2; ++k)
+        for (int b = 0; b < 2; ++b)
+          if (eig_nb[j][b] > 0)
+            launch_z2_gather_sym((const double*)c->Amat.p + mat_elem_off[2 * j + k], chij[j] * chij[j],
+                                 zi + gz_eig[j] + (b == 0 ? 0 : eig_nb[j][0]), eig_nb[j][b],
+                                 Ab + boff[j][k][b], s);
+    int* swb = (int*)c->sweeps.p + 2 * kMaxD;
+    for (size_t g = 0; g < sizes.size(); ++g) {
+      const long long o = grp_first[g].first;
+      if (eig_batch(Ab + o, Wb + o, Vb + o, sizes[g], grp_cnt[g], swb + grp_first[g].second) != 0)
+        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    }
+    SweepMerge sm;
+    sm.n = 2 * (d - 1);
+    for (int j = 1; j < d; ++j) {
+      const int n = chij[j] * chij[j];
+      const int* eb = zi + gz_eig[j] + n;
+      for (int k = 0; k < 2; ++k) {
+        const int mat = mat_of_leg[j] + k;
+        sm.a[mat] = eig_nb[j][0] > 0 ? bidx[j][k][0] : -1;
+        sm.b[mat] = eig_nb[j][1] > 0 ? bidx[j][k][1] : -1;
+        const double* w0 = eig_nb[j][0] > 0 ? Wb + boff[j][k][0] : nullptr;
+        const double* w1 = eig_nb[j][1] > 0 ? Wb + boff[j][k][1] : nullptr;
+        const double* v0 = eig_nb[j][0] > 0 ? Vb + boff[j][k][0] : nullptr;
+        const double* v1 = eig_nb[j][1] > 0 ? Vb + boff[j][k][1] : nullptr;
+        launch_z2_scatter_eig(w0, eig_nb[j][0], w1, eig_nb[j][1], eb, eb + n, n,
+                              (double*)c->W.p + mat_elem_off[2 * j + k], s);
+        launch_z2_scatter_eig(v0, eig_nb[j][0], v1, eig_nb[j][1], eb, eb + n, n,
+                              (double*)c->V.p + mat_elem_off[2 * j + k], s);
+      }
+    }
+    launch_z2_merge_sweeps(swb, sm, (int*)c->sweeps.p, s);
   }
 
   // ---- choice, truncation, gauge (Secs. 4.2.6-4.2.8)
@@ -762,7 +1014,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     launch_select((const double*)c->W.p + mat_elem_off[2 * j], (const double*)c->V.p + mat_elem_off[2 * j],
                   n, 0, nnew[j], (double*)c->lam.p + lam_off[j], (double*)c->U64.p + u_off[j],
                   (float*)c->U32.p + u_off[j], (LegResult*)c->legres.p + j,
-                  (int*)c->sweeps.p + (mat_of_leg[j] - grp_first_mat[grp_of[j]]), s);
+                  (int*)c->sweeps.p + mat_of_leg[j], s);
   }
 
   // ---- Z2 blocks at zero field: the parity of each new index is that of the rows
@@ -1392,7 +1644,7 @@ int hotrg_set_parity(hotrg_ctx* c, const int* parity) {
     sl.mask[k] = 0;
     for (int v = 0; v < c->chis[ax]; ++v) sl.mask[k] |= (unsigned)par[ax][v] << v;
   }
-  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (3 * 2 * kMaxD + 3)));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (kCounters32 + 3)));
   int* cnt = (int*)c->counters.p;
   int bad = 0;
   cudaMemsetAsync(cnt, 0, sizeof(int), c->stream);
@@ -1484,9 +1736,11 @@ void hotrg_free(hotrg_ctx* c) {
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  if (c->hpin_ev) cudaEventDestroy(c->hpin_ev);
   delete c;
 }
 

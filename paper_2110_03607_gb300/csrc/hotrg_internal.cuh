@@ -107,6 +107,18 @@ struct Z2Slots {
   unsigned mask[kMaxD];   // bit v: parity of index v of the slot
 };
 void launch_z2_check(const double* T, const Z2Slots& sl, long long total, int* count, cudaStream_t s);
+struct SweepMerge {
+  int n;
+  int a[2 * kMaxD], b[2 * kMaxD];
+};
+void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, double* Ab, cudaStream_t s);
+void launch_z2_scatter_eig(const double* m0, int n0, const double* m1, int n1, const int* blk,
+                           const int* pos, int n, double* M, cudaStream_t s);
+void launch_z2_merge_sweeps(const int* src, const SweepMerge& m, int* dst, cudaStream_t s);
+void launch_z2_gather_rc(const double* T, const long long* roff, int m, const long long* koff,
+                         long long K, double* X, cudaStream_t s);
+void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
+                          const int* blk, const int* pos, int m, double* S, cudaStream_t s);
 void launch_z2_gather_split(const double* src, long long ld, const int* rowmap, int nrows,
                             const int* colmap, int ncols, __nv_bfloat16* dst, long long piece_stride,
                             int npieces, cudaStream_t s);

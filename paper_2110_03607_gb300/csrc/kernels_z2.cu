@@ -158,4 +158,112 @@ void launch_z2_check(const double* T, const Z2Slots& sl, long long total, int* c
   ++g_launches;
 }
 
+// Environment Grams in parity blocks (Sec. 3.2): X[i][k] = T[roff[i] + koff[k]], with the
+// rows (n_j, current) and the summed index `rest` both listed even parity first, so that
+// X[(rows of parity b)][(columns of parity b)] is a contiguous block and the Gram is
+// block diagonal: S_b = X_b X_b^T.  One grid row per X row.
+__global__ void z2_gather_rc_kernel(const double* __restrict__ T, const long long* __restrict__ roff,
+                                    const long long* __restrict__ koff, long long K,
+                                    double* __restrict__ X) {
+  const long long ro = roff[blockIdx.y];
+  double* xr = X + (long long)blockIdx.y * K;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+       k += (long long)gridDim.x * blockDim.x)
+    xr[k] = T[ro + koff[k]];
+}
+
+void launch_z2_gather_rc(const double* T, const long long* roff, int m, const long long* koff,
+                         long long K, double* X, cudaStream_t s) {
+  long long bx = (K + 255) / 256;
+  const long long cap = (152LL * 16 + m - 1) / m;   // about 16 CTAs of 256 threads per SM
+  if (bx > cap) bx = cap;
+  if (bx < 1) bx = 1;
+  z2_gather_rc_kernel<<<dim3((unsigned)bx, (unsigned)m), 256, 0, s>>>(T, roff, koff, K, X);
+  ++g_launches;
+}
+
+// S[i][j] = sum_z parts_b[z][min(p_i, p_j)][max(p_i, p_j)] if rows i and j are both of
+// parity b (positions p_i, p_j in block b), else 0; parts_b holds ns_b split-K partials
+// of the upper triangle of the m_b x m_b block Gram.
+__global__ void z2_reduce_sym_kernel(const double* __restrict__ p0, int ns0, int m0,
+                                     const double* __restrict__ p1, int ns1, int m1,
+                                     const int* __restrict__ blk, const int* __restrict__ pos, int m,
+                                     double* __restrict__ S) {
+  const long long total = (long long)m * m;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e - (long long)i * m);
+    double acc = 0.0;
+    const int b = blk[i];
+    if (b == blk[j]) {
+      const int pi = pos[i], pj = pos[j];
+      const int lo = pi < pj ? pi : pj, hi = pi < pj ? pj : pi;
+      const double* p = b == 0 ? p0 : p1;
+      const int mb = b == 0 ? m0 : m1, ns = b == 0 ? ns0 : ns1;
+      const long long bb = (long long)mb * mb;
+      for (int z = 0; z < ns; ++z) acc += p[z * bb + (long long)lo * mb + hi];
+    }
+    S[e] = acc;
+  }
+}
+
+void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
+                          const int* blk, const int* pos, int m, double* S, cudaStream_t s) {
+  z2_reduce_sym_kernel<<<grid_for((long long)m * m), 256, 0, s>>>(p0, ns0, m0, p1, ns1, m1, blk, pos,
+                                                                  m, S);
+  ++g_launches;
+}
+
+// Eigen-decomposition in parity blocks (Sec. 4.2.5): A^(j) is block diagonal in the
+// parity of its composite index (hat, check), so each block is decomposed on its own.
+// Ab[p][q] = A[rows[p]][rows[q]] for p, q < nb
+__global__ void z2_gather_sym_kernel(const double* __restrict__ A, int n, const int* __restrict__ rows,
+                                     int nb, double* __restrict__ Ab) {
+  const int total = nb * nb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int p = e / nb, q = e - p * nb;
+    Ab[e] = A[(long long)rows[p] * n + rows[q]];
+  }
+}
+
+void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, double* Ab, cudaStream_t s) {
+  z2_gather_sym_kernel<<<grid_for((long long)nb * nb), 256, 0, s>>>(A, n, rows, nb, Ab);
+  ++g_launches;
+}
+
+// Column-major n x n M from the blocks: M[r + c n] = M_b[pos[r] + pos[c] n_b] if rows r
+// and c are both of parity b, else 0 (column c of M is column pos[c] of block blk[c])
+__global__ void z2_scatter_eig_kernel(const double* __restrict__ m0, int n0, const double* __restrict__ m1,
+                                      int n1, const int* __restrict__ blk, const int* __restrict__ pos,
+                                      int n, double* __restrict__ M) {
+  const int total = n * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int cidx = e / n, r = e - cidx * n;
+    const int b = blk[r];
+    double v = 0.0;
+    if (b == blk[cidx]) v = b == 0 ? m0[pos[r] + (long long)pos[cidx] * n0] : m1[pos[r] + (long long)pos[cidx] * n1];
+    M[e] = v;
+  }
+}
+
+void launch_z2_scatter_eig(const double* m0, int n0, const double* m1, int n1, const int* blk,
+                           const int* pos, int n, double* M, cudaStream_t s) {
+  z2_scatter_eig_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(m0, n0, m1, n1, blk, pos, n, M);
+  ++g_launches;
+}
+
+// dst[k] = max(src[a[k]], src[b[k]]) (b[k] < 0: src[a[k]] alone)
+__global__ void z2_merge_sweeps_kernel(const int* __restrict__ src, SweepMerge m, int* __restrict__ dst) {
+  const int k = threadIdx.x;
+  if (k >= m.n) return;
+  int v = m.a[k] >= 0 ? src[m.a[k]] : 0;
+  if (m.b[k] >= 0 && src[m.b[k]] > v) v = src[m.b[k]];
+  dst[k] = v;
+}
+
+void launch_z2_merge_sweeps(const int* src, const SweepMerge& m, int* dst, cudaStream_t s) {
+  z2_merge_sweeps_kernel<<<1, 32, 0, s>>>(src, m, dst);
+  ++g_launches;
+}
+
 }  // namespace hotrg
