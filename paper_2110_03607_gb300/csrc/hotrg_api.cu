@@ -928,17 +928,18 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
     }
   } else {
-    // A^(j), A'^(j) are block diagonal in the parity of (hat, check): gather the blocks,
-    // decompose each size group, scatter W and V back (zeros between parities)
+    // A^(j), A'^(j) are block diagonal in the parity of (hat, check): gather the blocks
+    // (both blocks of a leg zero-padded to the larger, so that one launch decomposes
+    // them), decompose each size group, scatter W and V back (zeros between parities)
     Phase ph(c, 2);
     const int* zi = (const int*)((const long long*)c->Zg.p + gz_n64);
     long long boff[kMaxD][2][2];
-    int bidx[kMaxD][2][2];
+    int bidx[kMaxD][2][2], npad[kMaxD];
     std::vector<int> sizes;
-    for (int j = 1; j < d; ++j)
-      for (int b = 0; b < 2; ++b)
-        if (eig_nb[j][b] > 0 && std::find(sizes.begin(), sizes.end(), eig_nb[j][b]) == sizes.end())
-          sizes.push_back(eig_nb[j][b]);
+    for (int j = 1; j < d; ++j) {
+      npad[j] = std::max(eig_nb[j][0], eig_nb[j][1]);
+      if (std::find(sizes.begin(), sizes.end(), npad[j]) == sizes.end()) sizes.push_back(npad[j]);
+    }
     long long eoff = 0;
     int nblk = 0;
     std::vector<std::pair<long long, int>> grp_first(sizes.size());   // element offset, block index
@@ -948,7 +949,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       for (int j = 1; j < d; ++j)
         for (int k = 0; k < 2; ++k)
           for (int b = 0; b < 2; ++b)
-            if (eig_nb[j][b] == sizes[g]) {
+            if (eig_nb[j][b] > 0 && npad[j] == sizes[g]) {
               boff[j][k][b] = eoff;
               bidx[j][k][b] = nblk++;
               eoff += (long long)sizes[g] * sizes[g];
@@ -964,7 +965,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         for (int b = 0; b < 2; ++b)
           if (eig_nb[j][b] > 0)
             launch_z2_gather_sym((const double*)c->Amat.p + mat_elem_off[2 * j + k], chij[j] * chij[j],
-                                 zi + gz_eig[j] + (b == 0 ? 0 : eig_nb[j][0]), eig_nb[j][b],
+                                 zi + gz_eig[j] + (b == 0 ? 0 : eig_nb[j][0]), eig_nb[j][b], npad[j],
                                  Ab + boff[j][k][b], s);
     int* swb = (int*)c->sweeps.p + 2 * kMaxD;
     for (size_t g = 0; g < sizes.size(); ++g) {
@@ -985,10 +986,8 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         const double* w1 = eig_nb[j][1] > 0 ? Wb + boff[j][k][1] : nullptr;
         const double* v0 = eig_nb[j][0] > 0 ? Vb + boff[j][k][0] : nullptr;
         const double* v1 = eig_nb[j][1] > 0 ? Vb + boff[j][k][1] : nullptr;
-        launch_z2_scatter_eig(w0, eig_nb[j][0], w1, eig_nb[j][1], eb, eb + n, n,
-                              (double*)c->W.p + mat_elem_off[2 * j + k], s);
-        launch_z2_scatter_eig(v0, eig_nb[j][0], v1, eig_nb[j][1], eb, eb + n, n,
-                              (double*)c->V.p + mat_elem_off[2 * j + k], s);
+        launch_z2_scatter_eig(w0, w1, npad[j], eb, eb + n, n, (double*)c->W.p + mat_elem_off[2 * j + k], s);
+        launch_z2_scatter_eig(v0, v1, npad[j], eb, eb + n, n, (double*)c->V.p + mat_elem_off[2 * j + k], s);
       }
     }
     launch_z2_merge_sweeps(swb, sm, (int*)c->sweeps.p, s);
@@ -1185,6 +1184,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
   }
   const int* zmap = (const int*)c->Zmap.p;
+  // the first non-prime stage reads the product's Z2 blocks directly (no dense C); the
+  // prime chain still writes a dense B, which is gathered into blocks: written in block
+  // order its stores land in partial sectors and the stage ran at half speed
+  const bool zfold = z2 && !fp64 && !c->f64_chains;
   const long long ldz = (maxL + 3) / 4 * 4;   // row pitch of the C blocks
   if (fp64) {
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Nsub * R));
@@ -1200,8 +1203,8 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   } else {
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
-    CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
     if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
+    if (!zfold) CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
     Phase ph(c, 4);
     if (z2) {
       CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(__nv_bfloat16) * npieces * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
@@ -1245,6 +1248,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
 
+  const void* cblk_cur[2] = {nullptr, nullptr};   // this sub-slice's C blocks (Z2)
   for (int sl = 0; sl < chi_c; ++sl)
   for (int n1lo = 0; n1lo < nnew1; n1lo += n1_chunk) {
     const int n1cnt = std::min(n1_chunk, nnew1 - n1lo);
@@ -1347,15 +1351,18 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         ldb_[b] = ldz;
         bn_done += 2.0 * (double)Rb[b] * (double)Nb * (double)Rb[b];
       }
-      Phase pg(c, 11);
-      if (fp64)
-        launch_z2_scatter_f64((const double*)cblk[0], ldb_[0], (const double*)cblk[1], ldb_[1],
-                              zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk, zmap + ch.off_pos,
-                              q, (int)R, (int)Nc, (double*)c->Cb.p, s);
-      else
-        launch_z2_scatter_f32((const float*)cblk[0], ldb_[0], (const float*)cblk[1], ldb_[1],
-                              zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk, zmap + ch.off_pos,
-                              q, (int)R, (int)Nc, (float*)c->Cb.p, s);
+      for (int b = 0; b < 2; ++b) cblk_cur[b] = cblk[b];
+      if (!zfold) {
+        Phase pg(c, 11);
+        if (fp64)
+          launch_z2_scatter_f64((const double*)cblk[0], ldb_[0], (const double*)cblk[1], ldb_[1],
+                                zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk,
+                                zmap + ch.off_pos, q, (int)R, (int)Nc, (double*)c->Cb.p, s);
+        else
+          launch_z2_scatter_f32((const float*)cblk[0], ldb_[0], (const float*)cblk[1], ldb_[1],
+                                zmap + moff_rowblk, zmap + moff_rowpos, zmap + ch.off_blk,
+                                zmap + ch.off_pos, q, (int)R, (int)Nc, (float*)c->Cb.p, s);
+      }
     } else {
     bn_done += 2.0 * (double)R * (double)Nc * (double)R;
     Phase ph(c, 6);
@@ -1371,8 +1378,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
     // -- non-prime chain, Eqs. (AfterBNNCD)-(AfterBN1), Eq. (Elements_NewTensor)
     View cin;
-    cin.push_back({I_C, chi_c, P * Nc});
-    for (int k = 1; k < d; ++k) cin.push_back({I_NH + k, chij[k], prod_after(chij, k) * Nc});
+    // folded Z2 blocks: packed strides (row of C) << 32 | (column of C)
+    const long long rsh = zfold ? (1LL << 32) : Nc;
+    cin.push_back({I_C, chi_c, P * rsh});
+    for (int k = 1; k < d; ++k) cin.push_back({I_NH + k, chij[k], prod_after(chij, k) * rsh});
     for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P});
     for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
     const void* csrc = c->Cb.p;
@@ -1404,6 +1413,18 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         launch_chain_f64(cd, (const double*)csrc, (const double*)c->U64.p + u_off[j], (double*)dst, s);
       } else if (c->f64_chains) {
         launch_chain_f64acc(cd, csrc, j == d - 1 ? 0 : 1, (const double*)c->U64.p + u_off[j], dst, OUT_F64, s);
+      } else if (zfold && j == d - 1) {
+        const Z2Chunk& ch = zch[n1lo / n1_chunk];
+        Z2In zi;
+        zi.rblk = zmap + moff_rowblk;
+        zi.rpos = zmap + moff_rowpos;
+        zi.cblk = zmap + ch.off_blk;
+        zi.cpos = zmap + ch.off_pos;
+        zi.q = c->par[to[0]][sl];
+        zi.c[0] = (const float*)cblk_cur[0];
+        zi.c[1] = (const float*)cblk_cur[1];
+        zi.ld = ldz;
+        launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       } else {
         launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       }

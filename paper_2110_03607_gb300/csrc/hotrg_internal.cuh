@@ -100,6 +100,20 @@ void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, cons
                          void* out, int out_mode, cudaStream_t s);
 enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2 };
 
+// First non-prime stage read straight from the Z2 blocks of the bottleneck's product C.
+// The stage's in strides are packed: (C row stride) << 32 | (C column stride).
+struct Z2In {
+  const int* rblk;   // per C row (c, n^): parity b
+  const int* rpos;   // per C row: position in block b
+  const int* cblk;   // per C column (n', n~) of this sub-slice: parity p_N
+  const int* cpos;   // per C column: position in the list of its parity
+  int q;             // parity of the c'-slice: row parity b pairs with p_N = b ^ q
+  const float* c[2]; // the blocks (null if empty)
+  long long ld;      // row pitch of the blocks
+};
+void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, int out_mode,
+                           cudaStream_t s);
+
 // ---- kernels_z2.cu
 struct Z2Slots {
   int d;
@@ -111,9 +125,10 @@ struct SweepMerge {
   int n;
   int a[2 * kMaxD], b[2 * kMaxD];
 };
-void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, double* Ab, cudaStream_t s);
-void launch_z2_scatter_eig(const double* m0, int n0, const double* m1, int n1, const int* blk,
-                           const int* pos, int n, double* M, cudaStream_t s);
+void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, int npad, double* Ab,
+                          cudaStream_t s);
+void launch_z2_scatter_eig(const double* m0, const double* m1, int ld, const int* blk, const int* pos,
+                           int n, double* M, cudaStream_t s);
 void launch_z2_merge_sweeps(const int* src, const SweepMerge& m, int* dst, cudaStream_t s);
 void launch_z2_gather_rc(const double* T, const long long* roff, int m, const long long* koff,
                          long long K, double* X, cudaStream_t s);

@@ -6,8 +6,7 @@
 // A stage is described by a ChainDesc (strides of every free index in the
 // input and output, strides of the contracted hat/check indices).  Each
 // thread owns one free multi-index and accumulates all chi_j^new outputs in
-// registers; U~^(j) sits in shared memory (rows padded by one word so that
-// lanes with different hat indices hit different banks).
+// registers; U~^(j) sits in shared memory (padded rows, see URow).
 #include "hotrg_internal.cuh"
 
 namespace hotrg {
@@ -15,13 +14,40 @@ namespace hotrg {
 __device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
 __device__ __forceinline__ __nv_bfloat16 to_bf16(double x) { return __double2bfloat16(x); }
 
-template <typename TIn, typename TAcc, int NN, int OUT>
+// Row pitch of U~ in shared memory.  FP32: NN + 4 words keeps every row 16-byte
+// aligned for float4 loads (one LDS.128 per four FMAs) and puts the rows of eight
+// consecutive hat indices (lanes of the prime side) on distinct bank groups.  FP64:
+// NN + 1 words, scalar loads.
+template <typename TAcc, int NN>
+struct URow {
+  static constexpr int ld = NN + 1;
+  __device__ __forceinline__ static void fma_row(TAcc x, const TAcc* ur, TAcc* acc) {
+#pragma unroll
+    for (int n = 0; n < NN; ++n) acc[n] = fma(x, ur[n], acc[n]);
+  }
+};
+template <int NN>
+struct URow<float, NN> {
+  static constexpr int ld = NN + 4;
+  __device__ __forceinline__ static void fma_row(float x, const float* ur, float* acc) {
+#pragma unroll
+    for (int n = 0; n < NN; n += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(ur + n);
+      acc[n] = fmaf(x, u.x, acc[n]);
+      acc[n + 1] = fmaf(x, u.y, acc[n + 1]);
+      acc[n + 2] = fmaf(x, u.z, acc[n + 2]);
+      acc[n + 3] = fmaf(x, u.w, acc[n + 3]);
+    }
+  }
+};
+
+template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
 __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
-                                                    const TAcc* __restrict__ U, void* out) {
+                                                    const TAcc* __restrict__ U, void* out, Z2In zi) {
   extern __shared__ __align__(16) unsigned char smem_u[];
   TAcc* us = reinterpret_cast<TAcc*>(smem_u);
   const int rows = d.chi * d.chi;
-  const int ld = NN + 1;
+  constexpr int ld = URow<TAcc, NN>::ld;
   for (int e = threadIdx.x; e < rows * NN; e += blockDim.x) {
     int r = e / NN, c = e % NN;
     us[r * ld + c] = c < d.nn ? U[r * d.ldu + c] : TAcc(0);
@@ -54,8 +80,31 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
       for (int b = 0; b < d.chi; ++b) {
         TAcc x = (TAcc)xa[(long long)b * d.kb_stride];
         const TAcc* ur = us + (a_val + b * d.chi) * ld;
+        URow<TAcc, NN>::fma_row(x, ur, acc);
+      }
+    } else if (ZIN) {
+      // non-prime side from the Z2 blocks of C: only columns of parity (row parity) ^ q
+      // are nonzero; same two-level sums
+      const long long row0 = in_off >> 32, kar = d.ka_stride >> 32;
+      const long long col0 = in_off & 0xffffffffLL;
+      for (int a = a_lo; a < a_hi; ++a) {
+        const long long row = row0 + a * kar;
+        const int rb = zi.rblk[row];
+        const float* cr = rb ? zi.c[1] : zi.c[0];
+        if (!cr) continue;
+        cr += (long long)zi.rpos[row] * zi.ld;
+        TAcc part[NN];
 #pragma unroll
-        for (int n = 0; n < NN; ++n) acc[n] = fma(x, ur[n], acc[n]);
+        for (int n = 0; n < NN; ++n) part[n] = TAcc(0);
+        for (int b = 0; b < d.chi; ++b) {
+          const long long col = col0 + b * d.kb_stride;
+          if ((zi.cblk[col] ^ zi.q) != rb) continue;
+          TAcc x = (TAcc)cr[zi.cpos[col]];
+          const TAcc* ur = us + (a + b * d.chi) * ld;
+          URow<TAcc, NN>::fma_row(x, ur, part);
+        }
+#pragma unroll
+        for (int n = 0; n < NN; ++n) acc[n] += part[n];
       }
     } else
     // non-prime side, chi^2 terms, summed in two levels: the chi terms over b go
@@ -68,8 +117,7 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
       for (int b = 0; b < d.chi; ++b) {
         TAcc x = (TAcc)xa[(long long)b * d.kb_stride];
         const TAcc* ur = us + (a + b * d.chi) * ld;
-#pragma unroll
-        for (int n = 0; n < NN; ++n) part[n] = fma(x, ur[n], part[n]);
+        URow<TAcc, NN>::fma_row(x, ur, part);
       }
 #pragma unroll
       for (int n = 0; n < NN; ++n) acc[n] += part[n];
@@ -101,16 +149,17 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
   }
 }
 
-template <typename TIn, typename TAcc, int NN, int OUT>
-static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, cudaStream_t s) {
-  size_t smem = (size_t)d.chi * d.chi * (NN + 1) * sizeof(TAcc);
+template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
+static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, cudaStream_t s,
+                       const Z2In& zi = Z2In{}) {
+  size_t smem = (size_t)d.chi * d.chi * URow<TAcc, NN>::ld * sizeof(TAcc);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT, ZIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   long long blocks = (d.total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  chain_kernel<TIn, TAcc, NN, OUT><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out);
+  chain_kernel<TIn, TAcc, NN, OUT, ZIN><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi);
   ++g_launches;
 }
 
@@ -130,6 +179,22 @@ static void dispatch_nn(const ChainDesc& d, const TIn* in, const TAcc* U, void* 
   else if (d.nn <= 16) dispatch_out<TIn, TAcc, 16>(d, in, U, out, out_mode, s);
   else if (d.nn <= 24) dispatch_out<TIn, TAcc, 24>(d, in, U, out, out_mode, s);
   else dispatch_out<TIn, TAcc, 32>(d, in, U, out, out_mode, s);
+}
+
+template <int OUT>
+static void dispatch_nn_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, cudaStream_t s) {
+  const float* none = nullptr;
+  if (d.nn <= 4) launch_one<float, float, 4, OUT, true>(d, none, U, out, s, zi);
+  else if (d.nn <= 8) launch_one<float, float, 8, OUT, true>(d, none, U, out, s, zi);
+  else if (d.nn <= 16) launch_one<float, float, 16, OUT, true>(d, none, U, out, s, zi);
+  else if (d.nn <= 24) launch_one<float, float, 24, OUT, true>(d, none, U, out, s, zi);
+  else launch_one<float, float, 32, OUT, true>(d, none, U, out, s, zi);
+}
+
+void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, int out_mode,
+                           cudaStream_t s) {
+  if (out_mode == OUT_F64) dispatch_nn_z2in<OUT_F64>(d, zi, U, out, s);
+  else dispatch_nn_z2in<OUT_F32>(d, zi, U, out, s);
 }
 
 void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U, void* out,

@@ -276,12 +276,16 @@ __global__ void __launch_bounds__(1024) jacobi32_block_kernel(const double* __re
   }
 }
 
-// Block size b (nb = ceil(n / b) even, 2b <= 64 pairs of warps) so that two
-// blocks of W and V fit in 200 KB of shared memory.
+// Block size b: four blocks (three outer rounds, one grid barrier each, per sweep) when
+// two blocks of W and V fit in 200 KB of shared memory, else b = 32 (or less) and
+// nb = ceil(n / b) rounded up to even.
 int launch_jacobi32_block(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
                           int* counters, cudaStream_t s) {
-  int b = 32;
-  while (b > 4 && (size_t)4 * b * n * sizeof(float) > 200 * 1024) b /= 2;
+  int b = (n + 3) / 4;
+  if (b > 64 || (size_t)4 * b * n * sizeof(float) > 200 * 1024) {
+    b = 32;
+    while (b > 4 && (size_t)4 * b * n * sizeof(float) > 200 * 1024) b /= 2;
+  }
   int nb = (n + b - 1) / b;
   if (nb & 1) ++nb;
   if (nb < 2) nb = 2;

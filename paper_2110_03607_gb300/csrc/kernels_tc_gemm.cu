@@ -38,7 +38,15 @@ struct TcTerms {
   int nterms;
   int pa[9];
   int pb[9];
+  int clen[9];   // K-blocks per accumulation chunk of each term
 };
+
+// chunks of term t: ceil(kblocks / clen[t])
+__device__ __forceinline__ int count_chunks(const TcTerms& terms, int kblocks) {
+  int n = 0;
+  for (int t = 0; t < terms.nterms; ++t) n += (kblocks + terms.clen[t] - 1) / terms.clen[t];
+  return n;
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -161,7 +169,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    float* __restrict__ C, int M, int N, long long ldc, int kblocks, TcTerms terms,
-                   int chunk_iters, int* g_err) {
+                   int* g_err) {
   extern __shared__ uint8_t smem_raw[];
   volatile int* gerr = g_err;
   if (*gerr) return;  // an earlier CTA gave up: do nothing
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   const int total = terms.nterms * kblocks;
-  const int nchunks = (total + chunk_iters - 1) / chunk_iters;
+  const int nchunks = count_chunks(terms, kblocks);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -241,13 +249,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16_f32(TM, TN);
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
+      int c = 0, t = 0, kb0 = 0;   // chunk c = K-blocks [kb0, kb0 + clen[t]) of term t
+      for (; c < nchunks && ok; ++c) {
         const int b = c & 1;
         if (c >= 2 && !mbar_wait(tempty + b, (uint32_t)((c >> 1) - 1) & 1u, cta_abort, gerr)) break;
         tc_fence_after();
         const uint32_t dst = tmem + (uint32_t)(b * TN);
-        const int it_end = min(total, (c + 1) * chunk_iters);
-        for (int it = c * chunk_iters; it < it_end; ++it) {
+        const int it_begin = t * kblocks + kb0;
+        const int it_end = t * kblocks + min(kblocks, kb0 + terms.clen[t]);
+        kb0 += terms.clen[t];
+        if (kb0 >= kblocks) {
+          kb0 = 0;
+          ++t;
+        }
+        for (int it = it_begin; it < it_end; ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
           if (!mbar_wait(full + s, ph, cta_abort, gerr)) {
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // advance 16 BF16 = 32 bytes along K inside the 128-byte swizzled row;
             // the first MMA of a chunk starts the buffer from zero
             umma_bf16(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
-                      (it != c * chunk_iters || kk != 0) ? 1u : 0u);
+                      (it != it_begin || kk != 0) ? 1u : 0u);
           }
           umma_commit(empty + s);
         }
@@ -358,9 +373,14 @@ static EncodeTiledFn get_encode() {
 
 int tc_gemm_ready() { return get_encode() != nullptr; }
 
-// K-blocks (of 64) accumulated in TMEM before the epilogue adds them into FP32
-// registers.  Tuning knob HOTRG_TC_CHUNK_KBLOCKS (default 2 = K chunks of 128:
-// the truncating tensor-core accumulation then spans 8 MMAs only).
+// K-blocks (of 64) of the leading term x_0 y_0 accumulated in TMEM before the
+// epilogue adds them into FP32 registers.  Tuning knob HOTRG_TC_CHUNK_KBLOCKS
+// (default 2 = K chunks of 128: the truncating tensor-core accumulation then
+// spans 8 MMAs only).  A term whose pieces sum to order 1 (x_1 y_0, x_0 y_1,
+// about 2^-8 of the leading term) takes chunks 8 times longer, and the smaller
+// terms (about 2^-16) the whole K at once: their truncation error, relative to
+// the result, stays below the leading term's, and the epilogue drains TMEM a
+// quarter as often.
 int tc_chunk_kblocks() {
   static int v = -1;
   if (v < 0) {
@@ -395,9 +415,13 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
   if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) return -1;
   TcTerms terms;
   terms.nterms = nterms;
+  const int kblocks = Kpad / TK, base = tc_chunk_kblocks();
   for (int t = 0; t < 9; ++t) {
     terms.pa[t] = t < nterms ? pa[t] : 0;
     terms.pb[t] = t < nterms ? pb[t] : 0;
+    const int order = terms.pa[t] + terms.pb[t];
+    terms.clen[t] = order == 0 ? base : order == 1 ? 8 * base : kblocks;
+    if (terms.clen[t] < 1) terms.clen[t] = 1;
   }
   static bool attr = false;
   if (!attr) {
@@ -411,8 +435,7 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, Kpad / TK, terms,
-                                                    tc_chunk_kblocks(), err_flag);
+  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, kblocks, terms, err_flag);
   ++g_launches;
   if (ms_out) {
     cudaEventRecord(e1, s);

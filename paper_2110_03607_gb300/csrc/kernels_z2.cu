@@ -47,40 +47,55 @@ __global__ void z2_gather_f64_kernel(const double* __restrict__ src, long long l
   }
 }
 
-// BF16 pieces: dst[p][i][j] = src[p][rowmap[i]][colmap[j]] (0 where colmap[j] < 0)
+// BF16 pieces: dst[p][i][j] = src[p][rowmap[i]][colmap[j]] (0 where colmap[j] < 0).
+// Rows over grid y, four consecutive columns per thread (ncols is a multiple of 4):
+// one 8-byte store per piece.
 __global__ void z2_gather_bf16_kernel(const __nv_bfloat16* __restrict__ src, long long ld,
                                       long long src_piece_stride, const int* __restrict__ rowmap,
                                       int nrows, const int* __restrict__ colmap, int ncols,
                                       __nv_bfloat16* __restrict__ dst, long long dst_piece_stride,
                                       int npieces) {
-  long long total = (long long)nrows * ncols;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(e / ncols), j = (int)(e - (long long)i * ncols);
-    int cj = colmap[j];
-    long long so = (long long)rowmap[i] * ld + cj;
-    for (int p = 0; p < npieces; ++p)
-      dst[p * dst_piece_stride + e] = cj >= 0 ? src[p * src_piece_stride + so] : zero;
+  const int nq = ncols >> 2;
+  for (int i = blockIdx.y; i < nrows; i += gridDim.y) {
+    const __nv_bfloat16* sr = src + (long long)rowmap[i] * ld;
+    __nv_bfloat16* dr = dst + (long long)i * ncols;
+    for (int jq = blockIdx.x * blockDim.x + threadIdx.x; jq < nq; jq += gridDim.x * blockDim.x) {
+      const int4 cm = reinterpret_cast<const int4*>(colmap)[jq];
+      for (int p = 0; p < npieces; ++p) {
+        const __nv_bfloat16* sp = sr + p * src_piece_stride;
+        __align__(8) __nv_bfloat16 v[4];
+        v[0] = cm.x >= 0 ? sp[cm.x] : __float2bfloat16(0.0f);
+        v[1] = cm.y >= 0 ? sp[cm.y] : __float2bfloat16(0.0f);
+        v[2] = cm.z >= 0 ? sp[cm.z] : __float2bfloat16(0.0f);
+        v[3] = cm.w >= 0 ? sp[cm.w] : __float2bfloat16(0.0f);
+        *reinterpret_cast<uint2*>(dr + p * dst_piece_stride + 4 * jq) = *reinterpret_cast<const uint2*>(v);
+      }
+    }
   }
 }
 
-// dense[r][n] = C_b[rowpos[r]][colpos[n]] if colpar[n] ^ q == rowpar[r] = b, else 0
+// dense[r][n] = C_b[rowpos[r]][colpos[n]] if colpar[n] ^ q == rowpar[r] = b, else 0.
+// Rows over grid y, four consecutive columns per thread.
 template <typename T>
 __global__ void z2_scatter_kernel(const T* __restrict__ c0, long long ld0, const T* __restrict__ c1,
                                   long long ld1, const int* __restrict__ rowblk,
                                   const int* __restrict__ rowpos, const int* __restrict__ colblk,
                                   const int* __restrict__ colpos, int q, int nrows, int ncols,
                                   T* __restrict__ dense) {
-  long long total = (long long)nrows * ncols;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e / ncols), n = (int)(e - (long long)r * ncols);
-    int b = rowblk[r];
-    const T* cb = b == 0 ? c0 : c1;   // null: the block is empty (no columns)
-    T v = T(0);
-    if ((colblk[n] ^ q) == b && cb) v = cb[(long long)rowpos[r] * (b == 0 ? ld0 : ld1) + colpos[n]];
-    dense[e] = v;
+  for (int r = blockIdx.y; r < nrows; r += gridDim.y) {
+    const int b = rowblk[r];
+    const T* cr = b == 0 ? c0 : c1;   // null: the block is empty (no columns)
+    if (cr) cr += (long long)rowpos[r] * (b == 0 ? ld0 : ld1);
+    T* dr = dense + (long long)r * ncols;
+    for (int n0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); n0 < ncols;
+         n0 += 4 * gridDim.x * blockDim.x) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = n0 + u;
+        if (n >= ncols) break;
+        dr[n] = ((colblk[n] ^ q) == b && cr) ? cr[colpos[n]] : T(0);
+      }
+    }
   }
 }
 
@@ -128,11 +143,23 @@ void launch_z2_gather_f64(const double* src, long long ld, const int* rowmap, in
   ++g_launches;
 }
 
+// rows over grid y (at most 65535, grid-stride beyond), columns over x
+static dim3 grid_rows(int nrows, long long units_per_row) {
+  long long bx = (units_per_row + 255) / 256;
+  if (bx < 1) bx = 1;
+  long long by = nrows < 1 ? 1 : nrows;
+  if (by > 65535) by = 65535;
+  // about 32 CTAs of 256 threads per SM in all
+  long long cap = (152LL * 32 + by - 1) / by;
+  if (bx > cap) bx = cap;
+  return dim3((unsigned)bx, (unsigned)by);
+}
+
 void launch_z2_gather_bf16(const __nv_bfloat16* src, long long ld, long long src_piece_stride,
                            const int* rowmap, int nrows, const int* colmap, int ncols,
                            __nv_bfloat16* dst, long long dst_piece_stride, int npieces,
                            cudaStream_t s) {
-  z2_gather_bf16_kernel<<<grid_for((long long)nrows * ncols), 256, 0, s>>>(
+  z2_gather_bf16_kernel<<<grid_rows(nrows, ncols / 4), 256, 0, s>>>(
       src, ld, src_piece_stride, rowmap, nrows, colmap, ncols, dst, dst_piece_stride, npieces);
   ++g_launches;
 }
@@ -140,7 +167,7 @@ void launch_z2_gather_bf16(const __nv_bfloat16* src, long long ld, long long src
 void launch_z2_scatter_f32(const float* c0, long long ld0, const float* c1, long long ld1,
                            const int* rowblk, const int* rowpos, const int* colblk, const int* colpos,
                            int q, int nrows, int ncols, float* dense, cudaStream_t s) {
-  z2_scatter_kernel<float><<<grid_for((long long)nrows * ncols), 256, 0, s>>>(
+  z2_scatter_kernel<float><<<grid_rows(nrows, (ncols + 3) / 4), 256, 0, s>>>(
       c0, ld0, c1, ld1, rowblk, rowpos, colblk, colpos, q, nrows, ncols, dense);
   ++g_launches;
 }
@@ -148,7 +175,7 @@ void launch_z2_scatter_f32(const float* c0, long long ld0, const float* c1, long
 void launch_z2_scatter_f64(const double* c0, long long ld0, const double* c1, long long ld1,
                            const int* rowblk, const int* rowpos, const int* colblk, const int* colpos,
                            int q, int nrows, int ncols, double* dense, cudaStream_t s) {
-  z2_scatter_kernel<double><<<grid_for((long long)nrows * ncols), 256, 0, s>>>(
+  z2_scatter_kernel<double><<<grid_rows(nrows, (ncols + 3) / 4), 256, 0, s>>>(
       c0, ld0, c1, ld1, rowblk, rowpos, colblk, colpos, q, nrows, ncols, dense);
   ++g_launches;
 }
@@ -216,39 +243,42 @@ void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, i
 
 // Eigen-decomposition in parity blocks (Sec. 4.2.5): A^(j) is block diagonal in the
 // parity of its composite index (hat, check), so each block is decomposed on its own.
-// Ab[p][q] = A[rows[p]][rows[q]] for p, q < nb
+// Ab[p][q] = A[rows[p]][rows[q]] for p, q < nb, zero-padded to npad x npad (a zero row and
+// column of A adds an exact zero column to W = A V that no rotation ever touches)
 __global__ void z2_gather_sym_kernel(const double* __restrict__ A, int n, const int* __restrict__ rows,
-                                     int nb, double* __restrict__ Ab) {
-  const int total = nb * nb;
+                                     int nb, int npad, double* __restrict__ Ab) {
+  const int total = npad * npad;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int p = e / nb, q = e - p * nb;
-    Ab[e] = A[(long long)rows[p] * n + rows[q]];
+    const int p = e / npad, q = e - p * npad;
+    Ab[e] = (p < nb && q < nb) ? A[(long long)rows[p] * n + rows[q]] : 0.0;
   }
 }
 
-void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, double* Ab, cudaStream_t s) {
-  z2_gather_sym_kernel<<<grid_for((long long)nb * nb), 256, 0, s>>>(A, n, rows, nb, Ab);
+void launch_z2_gather_sym(const double* A, int n, const int* rows, int nb, int npad, double* Ab,
+                          cudaStream_t s) {
+  z2_gather_sym_kernel<<<grid_for((long long)npad * npad), 256, 0, s>>>(A, n, rows, nb, npad, Ab);
   ++g_launches;
 }
 
-// Column-major n x n M from the blocks: M[r + c n] = M_b[pos[r] + pos[c] n_b] if rows r
-// and c are both of parity b, else 0 (column c of M is column pos[c] of block blk[c])
-__global__ void z2_scatter_eig_kernel(const double* __restrict__ m0, int n0, const double* __restrict__ m1,
-                                      int n1, const int* __restrict__ blk, const int* __restrict__ pos,
+// Column-major n x n M from the blocks (leading dimension ld): M[r + c n] =
+// M_b[pos[r] + pos[c] ld] if rows r and c are both of parity b, else 0 (column c of M is
+// column pos[c] of block blk[c]; the padding columns of the blocks are dropped)
+__global__ void z2_scatter_eig_kernel(const double* __restrict__ m0, const double* __restrict__ m1,
+                                      int ld, const int* __restrict__ blk, const int* __restrict__ pos,
                                       int n, double* __restrict__ M) {
   const int total = n * n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int cidx = e / n, r = e - cidx * n;
     const int b = blk[r];
     double v = 0.0;
-    if (b == blk[cidx]) v = b == 0 ? m0[pos[r] + (long long)pos[cidx] * n0] : m1[pos[r] + (long long)pos[cidx] * n1];
+    if (b == blk[cidx]) v = (b == 0 ? m0 : m1)[pos[r] + (long long)pos[cidx] * ld];
     M[e] = v;
   }
 }
 
-void launch_z2_scatter_eig(const double* m0, int n0, const double* m1, int n1, const int* blk,
-                           const int* pos, int n, double* M, cudaStream_t s) {
-  z2_scatter_eig_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(m0, n0, m1, n1, blk, pos, n, M);
+void launch_z2_scatter_eig(const double* m0, const double* m1, int ld, const int* blk, const int* pos,
+                           int n, double* M, cudaStream_t s) {
+  z2_scatter_eig_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(m0, m1, ld, blk, pos, n, M);
   ++g_launches;
 }
 
