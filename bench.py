@@ -54,6 +54,21 @@ D, CHI, BETA, H = W["d"], W["chi"], W["beta"], W["h"]
 FIRST_AXIS, GROWTH_STEPS = W["first"], W["growth"]
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (a plain float without a process group)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps_per_rank, world, elapsed_ms):
+    """Replicas: every rank runs its own steps; whole-job steps/s over the slowest rank."""
+    return world * steps_per_rank / (elapsed_ms / 1000.0)
+
+
 def select_workload(name):
     global W, WORKLOAD, D, CHI, BETA, H, FIRST_AXIS, GROWTH_STEPS
     W = dict(WORKLOADS[name])
@@ -307,12 +322,9 @@ def main():
     launches = pkg.hotrg_launch_count(g.ctx) - launches0
     sampler.stop()
     clocks = sampler.summary()
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     K = len(timed_axes)
-    value = world * K / (elapsed_ms / 1000.0)
+    value = whole_job_rate(K, world, elapsed_ms)
 
     # ---- accuracy against the FP64 oracle's per-step ln Z / V (tests/golden)
     golden = load_golden()
