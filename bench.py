@@ -47,7 +47,21 @@ WORKLOADS = {
                           text="4D Ising HOTRG d=4 chi=13 beta=0.15 h=0, axes x,y,z,w"),
     "ising4d_chi14": dict(d=4, chi=14, beta=0.15, h=0.0, first=0, growth=4,
                           text="4D Ising HOTRG d=4 chi=14 beta=0.15 h=0, axes x,y,z,w"),
+    # batching form: independent 3D instances, 16 per chi in {6, 8, 10, 12}, beta uniform
+    # in [0.20, 0.24], h alternating 0 / 0.01, stepped together
+    "batch3d_mixed": dict(d=3, chi=12, beta=0.22, h=0.0, first=2, growth=3,
+                          text="batching form: 64 independent 3D Ising HOTRG instances, chi in "
+                               "{6,8,10,12} x 16, beta uniform in [0.20,0.24], h in {0,0.01}, axes z,x,y"),
 }
+
+
+def batch_instances():
+    """(beta, h, chi) of the 64 instances of the batching form."""
+    out = []
+    for chi in (6, 8, 10, 12):
+        for i in range(16):
+            out.append((0.20 + 0.04 * i / 15.0, 0.0 if i % 2 == 0 else 0.01, chi))
+    return out
 W = dict(WORKLOADS["ising3d_chi16"])
 WORKLOAD = "ising3d_chi16"
 D, CHI, BETA, H = W["d"], W["chi"], W["beta"], W["h"]
@@ -243,6 +257,146 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def batch_arm(args):
+    """Batching form: 64 independent instances stepped together by hotrg_step_batch (one
+    stream and one host worker per instance in flight), against the same instances
+    stepped one after another.  Metric: instance-steps per second."""
+    import torch
+
+    import paper_2110_03607_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    inst = batch_instances()
+    n = len(inst)
+    streams = [torch.cuda.Stream() for _ in range(n)]
+    ctxs = []
+    for (beta, h, chi), st in zip(inst, streams):
+        c = pkg.hotrg_init_ising(3, beta, h)
+        pkg.hotrg_set_precision(c, prec)
+        pkg.hotrg_set_z2(c, args.z2 == "on")
+        pkg.hotrg_set_stream(c, st.cuda_stream)
+        ctxs.append(c)
+    chis = [x[2] for x in inst]
+    nthreads = args.batch_threads
+    total = GROWTH_STEPS + args.warmup + args.steps
+    axes = [(FIRST_AXIS + s) % D for s in range(total)]
+    for a in axes[: GROWTH_STEPS + args.warmup]:
+        pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
+    torch.cuda.synchronize()
+    timed = axes[GROWTH_STEPS + args.warmup:]
+    launches0 = pkg.hotrg_launch_count(ctxs[0])
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    flops = 0.0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a in timed:
+        pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
+    torch.cuda.synchronize()
+    elapsed_ms = (time.perf_counter() - t0) * 1000.0
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    launches = pkg.hotrg_launch_count(ctxs[0]) - launches0
+    for c in ctxs:
+        flops += pkg.hotrg_bottleneck_flops(c)[1]
+    lnz = [pkg.hotrg_free_energy(c)[0] for c in ctxs]
+    # the same instances, one after another (serial reference of the batching)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for a in axes[GROWTH_STEPS + args.warmup: GROWTH_STEPS + args.warmup + 2]:
+        for c, chi in zip(ctxs, chis):
+            pkg.hotrg_step(c, a, chi)
+        torch.cuda.synchronize()
+    serial_ms = (time.perf_counter() - t1) * 1000.0 / 2
+    # end to end: each instance's tensor from pinned host memory, one batch step, ln Z and
+    # the tensors back
+    e2e = None
+    if not args.no_e2e:
+        hosts, outs, dims, pars = [], [], [], []
+        for c in ctxs:
+            t = pkg.hotrg_tensor(c)
+            p = torch.empty(t.size, dtype=torch.float64, pin_memory=True)
+            p.numpy()[:] = t.reshape(-1)
+            hosts.append(p)
+            outs.append(torch.empty_like(p).pin_memory())
+            dims.append(pkg.hotrg_bond_dims(c)[:3])
+            pars.append(pkg.hotrg_leg_parity(c))
+        a = axes[-1]
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        h2d = d2h = 0
+        for c, p, dm, par in zip(ctxs, hosts, dims, pars):
+            pkg.hotrg_set_tensor(c, dm, p)
+            h2d += p.numel() * 8
+            if par is not None:
+                pkg.hotrg_set_parity(c, par)
+                h2d += 4 * len(par)
+        pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
+        for c, o in zip(ctxs, outs):
+            pkg.hotrg_free_energy(c)
+            pkg.hotrg_tensor(c, o.numpy().reshape([x for x in pkg.hotrg_bond_dims(c)[:3] for _ in (0, 1)]))
+            d2h += o.numel() * 8 + 16
+        e2e_s = time.perf_counter() - t2
+        e2e = {"value": n / e2e_s, "unit": "instance-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": 1}
+    clocks = sampler.summary()
+    for c in ctxs:
+        pkg.hotrg_free(c)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
+    K = len(timed)
+    value = whole_job_rate(n * K, world, elapsed_ms)
+    peaks, peak_src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    # flops: the performed bottleneck flops of one batch step (all instances' last step)
+    achieved = flops / (elapsed_ms / K / 1000.0) / 1e12 if K else None
+    if rank == 0:
+        line = {
+            "metric": "HOTRG instance-steps/s, batching form (64 independent 3D Ising instances)",
+            "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
+                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ",
+                      "fp64": "f64"}[args.precision],
+            "data": "synthetic (Ising initial tensors from beta, h; no dataset)",
+            "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
+                                   f"{args.warmup} warm-up steps, {K} timed batch steps",
+                       "precision": args.precision, "z2_blocks": args.z2 == "on",
+                       "host_workers": nthreads if nthreads > 0 else "hardware threads",
+                       "l2": "not flushed: the 64 instances' tensors and operands (several GB) "
+                             "exceed L2 together",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "serial_instance_steps_per_s": n / (serial_ms / 1000.0),
+            "batching_speedup": value / world / (n / (serial_ms / 1000.0)),
+            "ln_z_per_site_range": [min(lnz), max(lnz)],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                         "note": "whole-job bottleneck GEMM flops (performed) per batch step / "
+                                 "batch step wall time; kernels of different instances overlap"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,6 +407,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch-threads", type=int, default=16,
+                    help="host workers of the batching form (batch3d_mixed)")
     ap.add_argument("--z2", default="on", choices=["on", "off"],
                     help="Z2 block form of the contraction (on) or the paper's dense form (off)")
     args = ap.parse_args()
@@ -261,6 +417,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch3d_mixed":
+        return batch_arm(args)
 
     import torch
 

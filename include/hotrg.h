@@ -175,6 +175,19 @@ int hotrg_step_times(hotrg_ctx* ctx, double ms[16], int launches[16], int* n, in
  * ENOMEM, ECUDA, ESTATE. */
 int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
 
+/* Batching form: one coarse-graining step on each of n independent contexts
+ * (e.g. a scan over beta, h and chi), ctxs[i] along axes[i] with chis[i].
+ * Host threads (nthreads; <= 0: the hardware threads, at most n) each take the
+ * next context in turn, so the host-side waits of one context (the Z2 parity
+ * read-back) overlap the device work of the others; the contexts should have
+ * their own streams (hotrg_set_stream), else their kernels serialise on the
+ * shared stream.  Allocation hooks are called from these threads.  A context
+ * may appear once.  Returns the first failing status in index order (status[i],
+ * if given, receives each context's status).  Errors: EINVAL, and those of
+ * hotrg_step. */
+int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
+                     int* status);
+
 /* The isometry U~ chosen by the last step for lattice axis `leg` (a
  * transverse axis of that step): a rows x cols row-major FP64 matrix, rows
  * = chi_leg^2 indexed by (hat + check * chi_leg) (Sec. 3.2), cols =

@@ -69,6 +69,8 @@ def load():
         "hotrg_set_fp64_threshold": (I, [P, D]),
         "hotrg_set_slice_budget": (I, [P, D]),
         "hotrg_set_z2": (I, [P, I]),
+        "hotrg_step_batch": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I), I,
+                                 ctypes.POINTER(I)]),
         "hotrg_set_parity": (I, [P, ctypes.POINTER(I)]),
         "hotrg_leg_parity": (I, [P, ctypes.POINTER(I), I, ctypes.POINTER(I)]),
         "hotrg_bottleneck_flops": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
@@ -215,6 +217,17 @@ def hotrg_set_fp64_threshold(ctx, flops: float):
 
 def hotrg_set_slice_budget(ctx, nbytes: float):
     _check(load().hotrg_set_slice_budget(ctx, float(nbytes)), "hotrg_set_slice_budget")
+
+
+def hotrg_step_batch(ctxs, axes, chis, nthreads: int = 0):
+    """One step on each context, driven concurrently; returns the per-context statuses."""
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    ax = (ctypes.c_int * n)(*[int(a) for a in axes])
+    ch = (ctypes.c_int * n)(*[int(x) for x in chis])
+    st = (ctypes.c_int * n)()
+    _check(load().hotrg_step_batch(arr, n, ax, ch, int(nthreads), st), "hotrg_step_batch")
+    return [st[i] for i in range(n)]
 
 
 def hotrg_set_z2(ctx, enable: bool):

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "hotrg_internal.cuh"
@@ -286,14 +287,32 @@ void* pinned_stage(hotrg_ctx* c, size_t bytes) {
 constexpr int kCounters32 = 3 * 4 * kMaxD;
 
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n < 1) n = 148;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v < 1 ? 148 : v;
+  }();
   return n;
+}
+
+// A launch wrapper refused its arguments or the launch failed: report which, then the
+// CUDA error state (if any) decides the status
+int launch_failed(hotrg_ctx* c, const char* what, long long a, long long b, long long k) {
+  fprintf(stderr, "hotrg: %s launch failed (%lld, %lld, %lld)\n", what, a, b, k);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fprintf(stderr, "hotrg: CUDA error %s\n", cudaGetErrorString(e));
+  c->poisoned = HOTRG_ECUDA;
+  return HOTRG_ECUDA;
+}
+
+// A launch error left pending by the kernels of one part of the step: report the part
+int pending_error(hotrg_ctx* c, const char* part) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return HOTRG_OK;
+  fprintf(stderr, "hotrg: CUDA error after %s: %s\n", part, cudaGetErrorString(e));
+  c->poisoned = HOTRG_ECUDA;
+  return HOTRG_ECUDA;
 }
 
 int cuda_status(hotrg_ctx* c) {
@@ -880,6 +899,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                       (double*)c->Amat.p + mat_elem_off[2 * j + 1], s);
   }
 
+  if (pending_error(c, "the environments") != HOTRG_OK) return HOTRG_ECUDA;
   // ---- eigen-decomposition (Sec. 4.2.5), batched over matrices of equal size
   auto eig_batch = [&](const double* Ag, double* Wg, double* Vg, int n, int cnt, int* sweeps_out) -> int {
     const long long nn = (long long)n * n;
@@ -925,7 +945,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         }
       if (eig_batch((const double*)c->Amat.p + base, (double*)c->W.p + base, (double*)c->V.p + base,
                     grp_n[g], cnt, (int*)c->sweeps.p + grp_first_mat[g]) != 0)
-        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+        return launch_failed(c, "Jacobi", grp_n[g], cnt, 0);
     }
   } else {
     // A^(j), A'^(j) are block diagonal in the parity of (hat, check): gather the blocks
@@ -957,6 +977,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
             }
     }
     CHECK_ALLOC(dev_alloc(c, c->Eb, sizeof(double) * 3 * std::max<long long>(eoff, 1)));
+    // the warm start's scratch holds one size group: padded blocks can outgrow the dense
+    // matrices (4 npad^2 > 2 n^2 when one parity holds more than 0.707 of a leg's states)
+    CHECK_ALLOC(dev_alloc(c, c->J32, sizeof(float) * 2 * std::max<long long>(eoff, 1)));
+    CHECK_ALLOC(dev_alloc(c, c->Gns, sizeof(double) * std::max<long long>(eoff, 1)));
+    CHECK_ALLOC(dev_alloc(c, c->Vtmp, sizeof(double) * std::max<long long>(eoff, 1)));
     double* Ab = (double*)c->Eb.p;
     double* Wb = Ab + eoff;
     double* Vb = Wb + eoff;
@@ -971,7 +996,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     for (size_t g = 0; g < sizes.size(); ++g) {
       const long long o = grp_first[g].first;
       if (eig_batch(Ab + o, Wb + o, Vb + o, sizes[g], grp_cnt[g], swb + grp_first[g].second) != 0)
-        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+        return launch_failed(c, "Jacobi (Z2 blocks)", sizes[g], grp_cnt[g], 0);
     }
     SweepMerge sm;
     sm.n = 2 * (d - 1);
@@ -993,6 +1018,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     launch_z2_merge_sweeps(swb, sm, (int*)c->sweeps.p, s);
   }
 
+  if (pending_error(c, "the eigen-solver") != HOTRG_OK) return HOTRG_ECUDA;
   // ---- choice, truncation, gauge (Secs. 4.2.6-4.2.8)
   long long lam_total = 0, u_total = 0;
   long long lam_off[kMaxD], u_off[kMaxD];
@@ -1016,6 +1042,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                   (int*)c->sweeps.p + mat_of_leg[j], s);
   }
 
+  if (pending_error(c, "the selection") != HOTRG_OK) return HOTRG_ECUDA;
   // ---- Z2 blocks at zero field: the parity of each new index is that of the rows
   // its column of U occupies (every nonzero row of a column must agree; a column
   // that mixes parities ends the block treatment for the rest of the run)
@@ -1056,6 +1083,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
 
+  if (pending_error(c, "the parity read-back") != HOTRG_OK) return HOTRG_ECUDA;
   // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
   const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
   const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
@@ -1307,6 +1335,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       src_f64 = (fp64 || c->f64_chains) ? 1 : 0;
       in = out;
     }
+    if (pending_error(c, "the prime chain") != HOTRG_OK) return HOTRG_ECUDA;
     // -- bottleneck, Eq. (BottleneckPart): C[(c, n^)][(n', n~)] = T . B^T
     if (z2) {
       // blocks b = 0, 1: rows and K of parity b, columns of parity b ^ q
@@ -1345,7 +1374,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           if (launch_tc_gemm((const __nv_bfloat16*)c->Za.p + npieces * a_off, (int)Rb[b], zb, (int)Nb,
                              (int)Kpb[b], npieces, nterms, terms_a, terms_b, zc, ldz,
                              &((DevState*)c->state.p)->status, s, nullptr) != 0)
-            return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+            return launch_failed(c, "tensor-core GEMM (Z2 block)", Rb[b], Nb, Kpb[b]);
           cblk[b] = zc;
         }
         ldb_[b] = ldz;
@@ -1373,9 +1402,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
                          (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Nc,
                          &((DevState*)c->state.p)->status, s, nullptr) != 0)
-        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+        return launch_failed(c, "tensor-core GEMM", R, Nc, Kpad);
     }
     }
+    if (pending_error(c, "the bottleneck") != HOTRG_OK) return HOTRG_ECUDA;
     // -- non-prime chain, Eqs. (AfterBNNCD)-(AfterBN1), Eq. (Elements_NewTensor)
     View cin;
     // folded Z2 blocks: packed strides (row of C) << 32 | (column of C)
@@ -1424,7 +1454,16 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         zi.c[0] = (const float*)cblk_cur[0];
         zi.c[1] = (const float*)cblk_cur[1];
         zi.ld = ldz;
-        launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
+        const float* uj = (const float*)c->U32.p + u_off[j];
+        // output [rows of C without n^_j][columns without n~_j][n_j]: the layout of `out`
+        if (last || !launch_chain_nonprime_first(nullptr, Nc, &zi, R / chij[j], Nc / chij[j], chij[j],
+                                                 nnew[j], nnew[j], uj, (float*)dst, s))
+          launch_chain_f32_z2in(cd, zi, uj, dst, last ? OUT_F64 : OUT_F32, s);
+      } else if (!last && j == d - 1 &&
+                 launch_chain_nonprime_first((const float*)csrc, Nc, nullptr, R / chij[j], Nc / chij[j],
+                                             chij[j], nnew[j], nnew[j], (const float*)c->U32.p + u_off[j],
+                                             (float*)dst, s)) {
+        // dense C, first stage staged through shared memory
       } else {
         launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       }
@@ -1433,6 +1472,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
 
+  if (pending_error(c, "the non-prime chain") != HOTRG_OK) return HOTRG_ECUDA;
   // ---- bond dims of the new tensor (Sec. 4.2.15 with the axes kept physical)
   for (int j = 1; j < d; ++j) c->chis[to[j]] = nnew[j];
   if (track)
@@ -1635,6 +1675,36 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
   for (void* p : {dA, dB, dC, pA, pB, c32, (void*)err})
     if (p) cudaFree(p);
   return status;
+}
+
+int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
+                     int* status) {
+  if (n < 0 || (n > 0 && (!ctxs || !axes || !chis))) return HOTRG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return HOTRG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return HOTRG_EINVAL;   // one thread per context at a time
+  if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+  nthreads = std::min(nthreads, std::max(n, 1));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> st(n, HOTRG_OK);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next++; i < n; i = next++) st[i] = hotrg_step(ctxs[i], axes[i], chis[i]);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  int first = HOTRG_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = st[i];
+    if (first == HOTRG_OK) first = st[i];
+  }
+  return first;
 }
 
 int hotrg_set_z2(hotrg_ctx* c, int enable) {

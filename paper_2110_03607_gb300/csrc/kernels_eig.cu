@@ -132,14 +132,15 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
 template <int NPL>
 static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
                            int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
-  static int s_sms = -1, s_per_sm = 1;
-  if (s_sms < 0) {
-    int dev = 0;
+  // SM count and resident CTAs per SM, queried once (thread-safe static initialisation)
+  static const int2 occ = [] {
+    int dev = 0, sms = 0, per = 1;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&s_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s_per_sm, jacobi_onesided_kernel<NPL>, 256, 0);
-    if (s_per_sm < 1) s_per_sm = 1;
-  }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_onesided_kernel<NPL>, 256, 0);
+    return make_int2(sms, per < 1 ? 1 : per);
+  }();
+  const int s_sms = occ.x, s_per_sm = occ.y;
   int mp = n + (n & 1);
   int tasks = nmat * (mp / 2);
   // one block per SM (up to the task count): tasks are dealt round-robin over blocks

@@ -17,6 +17,7 @@
 // mbarrier wait is bounded in time; an expired wait sets a global error flag
 // that also makes the CTAs still to come exit at once.
 #include <cuda.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include "hotrg_internal.cuh"
@@ -357,17 +358,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -382,12 +381,11 @@ int tc_gemm_ready() { return get_encode() != nullptr; }
 // the result, stays below the leading term's, and the epilogue drains TMEM a
 // quarter as often.
 int tc_chunk_kblocks() {
-  static int v = -1;
-  if (v < 0) {
+  static const int v = [] {
     const char* e = getenv("HOTRG_TC_CHUNK_KBLOCKS");
-    v = e ? atoi(e) : 2;
-    if (v < 1) v = 1;
-  }
+    const int x = e ? atoi(e) : 2;
+    return x < 1 ? 1 : x;
+  }();
   return v;
 }
 
@@ -403,14 +401,29 @@ static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : -1;
+  if (r != CUDA_SUCCESS) {
+    fprintf(stderr, "hotrg: tensor map encoding failed (CUresult %d; rows %d, kpad %d)\n", (int)r, rows,
+            kpad);
+    return -1;
+  }
+  return 0;
 }
 
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb, float* C, long long ldc,
                    int* err_flag, cudaStream_t s, float* ms_out) {
-  if (Kpad % TK != 0 || nterms < 1 || nterms > 9) return -1;
-  if ((((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) return -1;
+  if (Kpad % TK != 0 || nterms < 1 || nterms > 9 || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
+    fprintf(stderr, "hotrg: GEMM arguments rejected (Kpad %d, terms %d, A %p, B %p)\n", Kpad, nterms,
+            (const void*)A, (const void*)B);
+    return -1;
+  }
+  {
+    const cudaError_t pre = cudaGetLastError();
+    if (pre != cudaSuccess) {
+      fprintf(stderr, "hotrg: CUDA error pending before the GEMM launch: %s\n", cudaGetErrorString(pre));
+      return -1;
+    }
+  }
   CUtensorMap ma, mb;
   if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) return -1;
   TcTerms terms;
@@ -423,11 +436,9 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
     terms.clen[t] = order == 0 ? base : order == 1 ? 8 * base : kblocks;
     if (terms.clen[t] < 1) terms.clen[t] = 1;
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
+  static const bool attr = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                SMEM_BYTES) == cudaSuccess;
+  (void)attr;
   dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ms_out) {
@@ -444,7 +455,12 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "hotrg: GEMM launch error %s (grid %u x %u)\n", cudaGetErrorString(e), grid.x, grid.y);
+    return -1;
+  }
+  return 0;
 }
 
 }  // namespace hotrg

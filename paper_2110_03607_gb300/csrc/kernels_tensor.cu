@@ -8,7 +8,7 @@
 
 namespace hotrg {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
 
 // T0 in the slot layout rows (x_0 .. x_{d-1}) x cols (x_0' .. x_{d-1}').
 // Every leg carries X_{s j}: X_{s 0} = sqrt(cosh b), X_{s 1} = sigma_s sqrt(sinh b)

@@ -252,3 +252,28 @@ def test_ising3d_chi16_sampled_new_tensor_elements_z2(pkg):
             np.testing.assert_allclose(got, slab, rtol=0, atol=2e-6 * scale)
     finally:
         pkg.hotrg_free(ctx)
+
+
+def test_unbalanced_parities_match_the_dense_form(pkg):
+    # 3D chi=12 at beta = 0.20 keeps mostly even states after a few steps: the padded
+    # eigen blocks then outgrow the dense matrices (one parity holds more than 0.707 of
+    # a leg's composite states).  The Z2 run must agree with the dense run (FP64 form).
+    d, chi, nsteps = 3, 12, 8
+    ga = pkg.Hotrg(d, 0.20, 0.0, precision=pkg.PREC_FP64, z2=True)
+    gb = pkg.Hotrg(d, 0.20, 0.0, precision=pkg.PREC_FP64, z2=False)
+    worst = 0.0
+    try:
+        for a in o.cyclic_axes(d, nsteps):
+            ga.step(a, chi)
+            gb.step(a, chi)
+            la, lb = ga.free_energy()[0], gb.free_energy()[0]
+            assert abs(la - lb) <= 1e-13 * abs(lb)
+            dims = pkg.hotrg_bond_dims(ga.ctx)[:d]
+            for p in _split_parity(pkg.hotrg_leg_parity(ga.ctx), dims):
+                e = int((p == 0).sum())
+                # share of the even composite (hat, check) states of this leg
+                worst = max(worst, (e * e + (len(p) - e) ** 2) / len(p) ** 2)
+        assert worst > 0.75, worst   # the padded case was exercised
+    finally:
+        ga.close()
+        gb.close()
