@@ -1454,16 +1454,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         zi.c[0] = (const float*)cblk_cur[0];
         zi.c[1] = (const float*)cblk_cur[1];
         zi.ld = ldz;
-        const float* uj = (const float*)c->U32.p + u_off[j];
-        // output [rows of C without n^_j][columns without n~_j][n_j]: the layout of `out`
-        if (last || !launch_chain_nonprime_first(nullptr, Nc, &zi, R / chij[j], Nc / chij[j], chij[j],
-                                                 nnew[j], nnew[j], uj, (float*)dst, s))
-          launch_chain_f32_z2in(cd, zi, uj, dst, last ? OUT_F64 : OUT_F32, s);
-      } else if (!last && j == d - 1 &&
-                 launch_chain_nonprime_first((const float*)csrc, Nc, nullptr, R / chij[j], Nc / chij[j],
-                                             chij[j], nnew[j], nnew[j], (const float*)c->U32.p + u_off[j],
-                                             (float*)dst, s)) {
-        // dense C, first stage staged through shared memory
+        launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       } else {
         launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       }

@@ -113,12 +113,6 @@ struct Z2In {
   const float* c[2]; // the blocks (null if empty)
   long long ld;      // row pitch of the blocks
 };
-// First non-prime stage staged through shared memory (FP32 in and out; C dense
-// [rows][ncols], or its Z2 blocks when zi is given); output Y[rr][nc][n], rr = rows of C
-// without the last hat index, nc = columns without the last check index.  false if the
-// shape is outside its limits (chi <= 16, nn <= 16), and then nothing was launched.
-bool launch_chain_nonprime_first(const float* C, long long ncols, const Z2In* zi, long long nrr, long long nnc,
-                                 int chi, int nn, int ldu, const float* U, float* Y, cudaStream_t s);
 void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, int out_mode,
                            cudaStream_t s);
 

@@ -216,120 +216,4 @@ void launch_chain_f64(const ChainDesc& d, const double* in, const double* U, dou
   dispatch_nn<double, double>(d, in, U, out, OUT_F64, s);
 }
 
-// ---------------------------------------------------------------------------
-// First non-prime stage, Eq. (AfterBNNCD), staged through shared memory:
-//   Y[rr][nc][n] = sum_a ( sum_b C[rr chi + a][nc chi + b] U~[(a + b chi)][n] ),
-// rr over the rows of C without the last hat index a, nc over its columns without the
-// last check index b.  A CTA owns one rr and 256 consecutive nc (one thread each, all
-// nn <= NN outputs in registers).  For each a it copies the contiguous row segment
-// C[rr chi + a][nc0 chi .. (nc0 + 256) chi) into shared memory (coalesced; from the Z2
-// blocks through the row and column maps, zeros outside them), then every thread sums
-// its chi entries against U~, whose row (a + b chi) all threads read at once (broadcast).
-// The b sums go into a fresh partial that is added once per a (as the generic stage).
-// ---------------------------------------------------------------------------
-template <int NN, bool Z2>
-__global__ void __launch_bounds__(256, 2) nonprime_first_smem_kernel(const float* __restrict__ C,
-                                                                  long long ncols, Z2In zi, long long nnc,
-                                                                  int chi, int nn, int ldu,
-                                                                  const float* __restrict__ U,
-                                                                  float* __restrict__ Y) {
-  extern __shared__ __align__(16) float np_smem[];
-  const int pitch = chi + 1;                  // per-thread row of the tile (bank-conflict free)
-  float* us = np_smem;                        // [chi * chi][NN]
-  float* tile = np_smem + chi * chi * NN;     // [256][chi + 1]
-  const int rows = chi * chi;
-  for (int e = threadIdx.x; e < rows * NN; e += blockDim.x) {
-    const int r = e / NN, cc = e - r * NN;
-    us[e] = cc < nn ? U[r * ldu + cc] : 0.0f;
-  }
-  const long long tiles_per_rr = (nnc + 255) / 256;
-  const long long rr = blockIdx.x / tiles_per_rr;
-  const long long nc0 = (blockIdx.x - rr * tiles_per_rr) * 256;
-  const int nvec = (int)min(256LL, nnc - nc0);
-  const int t = threadIdx.x;
-  float acc[NN];
-#pragma unroll
-  for (int n = 0; n < NN; ++n) acc[n] = 0.0f;
-  const long long col0 = nc0 * chi;
-  const int seg = nvec * chi;
-  for (int a = 0; a < chi; ++a) {
-    __syncthreads();   // the previous a's tile is no longer read (and U is in place)
-    const long long r = rr * chi + a;
-    if (Z2) {
-      const int rb = zi.rblk[r];
-      const float* cr = rb ? zi.c[1] : zi.c[0];
-      const long long rbase = cr ? (long long)zi.rpos[r] * zi.ld : 0;
-      for (int e = t; e < seg; e += blockDim.x) {
-        const long long col = col0 + e;
-        float x = 0.0f;
-        if (cr && (zi.cblk[col] ^ zi.q) == rb) x = cr[rbase + zi.cpos[col]];
-        const int tv = e / chi;
-        tile[tv * pitch + (e - tv * chi)] = x;
-      }
-    } else {
-      const float* cr = C + r * ncols + col0;
-      for (int e = t; e < seg; e += blockDim.x) {
-        const int tv = e / chi;
-        tile[tv * pitch + (e - tv * chi)] = cr[e];
-      }
-    }
-    __syncthreads();
-    if (t < nvec) {
-      float part[NN];
-#pragma unroll
-      for (int n = 0; n < NN; ++n) part[n] = 0.0f;
-      const float* xr = tile + t * pitch;
-      for (int b = 0; b < chi; ++b) {
-        const float x = xr[b];
-        const float* ur = us + (a + b * chi) * NN;
-#pragma unroll
-        for (int n = 0; n < NN; n += 4) {
-          const float4 u = *reinterpret_cast<const float4*>(ur + n);
-          part[n] = fmaf(x, u.x, part[n]);
-          part[n + 1] = fmaf(x, u.y, part[n + 1]);
-          part[n + 2] = fmaf(x, u.z, part[n + 2]);
-          part[n + 3] = fmaf(x, u.w, part[n + 3]);
-        }
-      }
-#pragma unroll
-      for (int n = 0; n < NN; ++n) acc[n] += part[n];
-    }
-  }
-  if (t < nvec) {
-    float* y = Y + ((rr * nnc) + nc0 + t) * nn;
-#pragma unroll
-    for (int n = 0; n < NN; ++n)
-      if (n < nn) y[n] = acc[n];
-  }
-}
-
-template <int NN>
-static void launch_np_first_t(const float* C, long long ncols, const Z2In* zi, long long nrr, long long nnc,
-                              int chi, int nn, int ldu, const float* U, float* Y, cudaStream_t s) {
-  const size_t smem = ((size_t)chi * chi * NN + (size_t)256 * (chi + 1)) * sizeof(float);
-  const long long blocks = nrr * ((nnc + 255) / 256);
-  if (zi) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(nonprime_first_smem_kernel<NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-    nonprime_first_smem_kernel<NN, true><<<(unsigned)blocks, 256, smem, s>>>(C, ncols, *zi, nnc, chi, nn, ldu,
-                                                                             U, Y);
-  } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(nonprime_first_smem_kernel<NN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-    nonprime_first_smem_kernel<NN, false><<<(unsigned)blocks, 256, smem, s>>>(C, ncols, Z2In{}, nnc, chi, nn,
-                                                                              ldu, U, Y);
-  }
-  ++g_launches;
-}
-
-bool launch_chain_nonprime_first(const float* C, long long ncols, const Z2In* zi, long long nrr, long long nnc,
-                                 int chi, int nn, int ldu, const float* U, float* Y, cudaStream_t s) {
-  if (chi > 16 || nn > 16 || nrr * ((nnc + 255) / 256) >= (1LL << 31)) return false;
-  if (nn <= 8) launch_np_first_t<8>(C, ncols, zi, nrr, nnc, chi, nn, ldu, U, Y, s);
-  else launch_np_first_t<16>(C, ncols, zi, nrr, nnc, chi, nn, ldu, U, Y, s);
-  return true;
-}
-
 }  // namespace hotrg
