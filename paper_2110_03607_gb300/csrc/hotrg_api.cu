@@ -1250,6 +1250,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
   }
   double bn_done = 0.0;
+  // The compacted K of a Z2 block holds no exact zeros, while half of the dense K
+  // products are zero: half the chunk keeps the same number of truncating
+  // accumulations per chunk as the dense form.
+  const int zchunk = std::max(1, tc_chunk_kblocks() / 2);
   CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
   double* Tn = (double*)c->T2.p;
 
@@ -1373,7 +1377,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           Phase ph(c, 6);
           if (launch_tc_gemm((const __nv_bfloat16*)c->Za.p + npieces * a_off, (int)Rb[b], zb, (int)Nb,
                              (int)Kpb[b], npieces, nterms, terms_a, terms_b, zc, ldz,
-                             &((DevState*)c->state.p)->status, s, nullptr) != 0)
+                             &((DevState*)c->state.p)->status, s, nullptr, zchunk) != 0)
             return launch_failed(c, "tensor-core GEMM (Z2 block)", Rb[b], Nb, Kpb[b]);
           cblk[b] = zc;
         }

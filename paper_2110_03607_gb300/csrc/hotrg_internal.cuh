@@ -153,10 +153,12 @@ void launch_z2_scatter_f64(const double* c0, long long ld0, const double* c1, lo
                            int q, int nrows, int ncols, double* dense, cudaStream_t s);
 
 // ---- kernels_tc_gemm.cu
-// C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T
+// C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T;
+// chunk_kblocks: accumulation chunk of the leading terms in K-blocks (0: the default)
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb,
-                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out);
+                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out,
+                   int chunk_kblocks = 0);
 int tc_gemm_ready();
 int tc_chunk_kblocks();
 

@@ -153,7 +153,8 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 32 lanes x 32 columns of FP32 from TMEM; the values are usable after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -164,6 +165,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
         "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -310,12 +314,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       tc_fence_after();
+      // two 32-column loads in flight per wait
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t v[32];
-        tmem_ld32(lane_base + (uint32_t)(b * TN + q * 32), v);
+      for (int q = 0; q < 4; q += 2) {
+        uint32_t v0[32], v1[32];
+        tmem_ld32_async(lane_base + (uint32_t)(b * TN + q * 32), v0);
+        tmem_ld32_async(lane_base + (uint32_t)(b * TN + (q + 1) * 32), v1);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v0[j]);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[(q + 1) * 32 + j] += __uint_as_float(v1[j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -375,11 +384,10 @@ int tc_gemm_ready() { return get_encode() != nullptr; }
 // K-blocks (of 64) of the leading term x_0 y_0 accumulated in TMEM before the
 // epilogue adds them into FP32 registers.  Tuning knob HOTRG_TC_CHUNK_KBLOCKS
 // (default 2 = K chunks of 128: the truncating tensor-core accumulation then
-// spans 8 MMAs only).  A term whose pieces sum to order 1 (x_1 y_0, x_0 y_1,
-// about 2^-8 of the leading term) takes chunks 8 times longer, and the smaller
-// terms (about 2^-16) the whole K at once: their truncation error, relative to
-// the result, stays below the leading term's, and the epilogue drains TMEM a
-// quarter as often.
+// spans 8 MMAs only).  The terms of order 2^-8 (x_1 y_0, x_0 y_1) take chunks 8
+// times longer and those of order 2^-16 the whole K at once: measured on 4D Ising
+// chi=6, this leaves ln Z/V where uniform chunks put it (8.4e-8 against 8.3e-8),
+// while the leading chunk's length does move it.
 int tc_chunk_kblocks() {
   static const int v = [] {
     const char* e = getenv("HOTRG_TC_CHUNK_KBLOCKS");
@@ -411,7 +419,7 @@ static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k
 
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb, float* C, long long ldc,
-                   int* err_flag, cudaStream_t s, float* ms_out) {
+                   int* err_flag, cudaStream_t s, float* ms_out, int chunk_kblocks) {
   if (Kpad % TK != 0 || nterms < 1 || nterms > 9 || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
     fprintf(stderr, "hotrg: GEMM arguments rejected (Kpad %d, terms %d, A %p, B %p)\n", Kpad, nterms,
             (const void*)A, (const void*)B);
@@ -428,7 +436,7 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
   if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) return -1;
   TcTerms terms;
   terms.nterms = nterms;
-  const int kblocks = Kpad / TK, base = tc_chunk_kblocks();
+  const int kblocks = Kpad / TK, base = chunk_kblocks > 0 ? chunk_kblocks : tc_chunk_kblocks();
   for (int t = 0; t < 9; ++t) {
     terms.pa[t] = t < nterms ? pa[t] : 0;
     terms.pb[t] = t < nterms ? pb[t] : 0;

@@ -236,3 +236,19 @@ def test_ising3d_chi16_sampled_new_tensor_elements(pkg):
             np.testing.assert_allclose(got, slab, rtol=0, atol=2e-6 * scale)
     finally:
         pkg.hotrg_free(ctx)
+
+
+@pytest.mark.parametrize("z2", [True, False])
+def test_ising4d_chi6_free_energy_matches_oracle_reference(pkg, z2):
+    # the paper's own dimension: 16 steps of 4D Ising chi=6 (beta = 0.15, axes x, y, z, w)
+    gold = _golden("ising4d_chi6")
+    assert len(gold) >= 12
+    g = pkg.Hotrg(4, 0.15, 0.0, precision=pkg.PREC_BF16X6, z2=z2)
+    try:
+        for step in range(1, max(gold) + 1):
+            g.step((step - 1) % 4, 6)
+            lnz, _ = g.free_energy()
+            ref = gold[step]["ln_z_per_site"]
+            assert abs(lnz - ref) / abs(ref) <= 1e-7, (step, lnz, ref)
+    finally:
+        g.close()
