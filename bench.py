@@ -504,8 +504,15 @@ def main():
                 "frac": achieved / 1.25 if achieved else None, "traffic": None,
                 "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
     else:
+        # DRAM bytes (read + write) of one Z2 block GEMM launch from the ncu capture in
+        # profiles/tc_gemm_kernel_ising3d_chi16_bf16x6.md (launch shape of the first steady
+        # steps: M = K = 2048, N = 32768); only for that workload and form
+        traffic = (0.655e9 + 0.302e9) if (WORKLOAD == "ising3d_chi16" and args.precision == "bf16x6"
+                                          and args.z2 == "on") else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_note": "bytes per launch at the step-4..7 launch shape (M=K=2048, N=32768); "
+                                "later steps have unequal blocks" if traffic else None,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}",
                 "issued_tflops": achieved * nterms if achieved else None,
                 "issued_frac": achieved * nterms / peak if achieved else None,
