@@ -697,7 +697,34 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     mmax = std::max<long long>(mmax, (long long)chij[j] * chi_c);
     nmax = std::max<long long>(nmax, (long long)chij[j] * chij[j]);
   }
-  const int nsplit_max = 128;
+  const int nsplit_max = 256;
+  // split-K count of a Gram (upper tiles of an m x m product over K): the CTAs that share
+  // an SM share its FP64 units, so the step lasts as long as the busiest SM's K-work.
+  // Among the splits that give at least two CTAs per SM (to hide latency; fewer only if
+  // K is too short), pick the one that minimises (CTAs on the busiest SM) x (K per CTA
+  // + a fixed cost).
+  auto gram_splits = [&](long long m, long long K) {
+    const long long ut = ((m + 63) / 64) * ((m + 63) / 64 + 1) / 2;
+    const long long sms = num_sms();
+    int best = 1, best_any = 1;
+    double best_cost = 1e300, best_any_cost = 1e300;
+    for (int ns = 1; ns <= nsplit_max; ++ns) {
+      long long kchunk = (K + ns - 1) / ns;
+      kchunk = (kchunk + 15) / 16 * 16;
+      if (kchunk < 64 && ns > 1) break;
+      const long long used = (K + kchunk - 1) / kchunk;
+      const double cost = (double)((ut * used + sms - 1) / sms) * (double)(kchunk + 64);
+      if (cost < best_any_cost * 0.999) {
+        best_any_cost = cost;
+        best_any = ns;
+      }
+      if (ut * used >= 2 * sms && cost < best_cost * 0.999) {
+        best_cost = cost;
+        best = ns;
+      }
+    }
+    return best_cost < 1e300 ? best : best_any;
+  };
   CHECK_ALLOC(dev_alloc(c, c->parts, sizeof(double) * nsplit_max * mmax * mmax));
   CHECK_ALLOC(dev_alloc(c, c->S, sizeof(double) * 4 * nlegs * mmax * mmax));
   CHECK_ALLOC(dev_alloc(c, c->Amat, sizeof(double) * total_mat_elems));
@@ -861,10 +888,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           const long long mb = gz_mb[j][b], Kb = gz_Kb[j][kind][b];
           if (mb == 0 || Kb == 0) continue;
           const long long r0 = b == 0 ? 0 : gz_mb[j][0], k0 = b == 0 ? 0 : gz_Kb[j][kind][0];
-          const int tiles = (int)((mb + 63) / 64);
-          const int upper_tiles = tiles * (tiles + 1) / 2;
-          int nsplit = std::max(1, std::min<int>(nsplit_max, (4 * num_sms()) / upper_tiles));
-          nsplit = (int)std::min<long long>(nsplit, std::max<long long>(1, Kb / 64));
+          const int nsplit = gram_splits(mb, Kb);
           double* pdst = (double*)c->parts.p + poff;
           launch_gemm_nt_f64(X + r0 * K + k0, K, X + r0 * K + k0, K, pdst, mb, mb * mb, (int)mb, (int)mb,
                              Kb, nsplit, 1, s);
@@ -880,11 +904,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         continue;
       }
       launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
-      // fill every SM with the same number of CTAs: tiles x splits <= 4 per SM
-      int tiles = (int)((m + 63) / 64);
-      int upper_tiles = tiles * (tiles + 1) / 2;
-      int nsplit = std::max(1, std::min<int>(nsplit_max, (4 * num_sms() ) / upper_tiles));
-      nsplit = (int)std::min<long long>(nsplit, std::max<long long>(1, K / 64));
+      const int nsplit = gram_splits(m, K);
       launch_gemm_nt_f64((const double*)c->Xp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p,
                          m, m * m, (int)m, (int)m, K, nsplit, 1, s);
       // the GEMM may round nsplit down; recompute the same way
