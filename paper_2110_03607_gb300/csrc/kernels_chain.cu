@@ -87,6 +87,21 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
       // are nonzero; same two-level sums
       const long long row0 = in_off >> 32, kar = d.ka_stride >> 32;
       const long long col0 = in_off & 0xffffffffLL;
+      // the column maps do not depend on a: for chi <= 16 read them once, packed as
+      // position | (block of the column) << 31
+      unsigned cpk[16];
+      const bool hoist = d.chi <= 16;
+      if (hoist) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          if (b < d.chi) {
+            const long long col = col0 + b * d.kb_stride;
+            cpk[b] = (unsigned)zi.cpos[col] | ((unsigned)(zi.cblk[col] ^ zi.q) << 31);
+          } else {
+            cpk[b] = 0u;
+          }
+        }
+      }
       for (int a = a_lo; a < a_hi; ++a) {
         const long long row = row0 + a * kar;
         const int rb = zi.rblk[row];
@@ -96,12 +111,22 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
         TAcc part[NN];
 #pragma unroll
         for (int n = 0; n < NN; ++n) part[n] = TAcc(0);
-        for (int b = 0; b < d.chi; ++b) {
-          const long long col = col0 + b * d.kb_stride;
-          if ((zi.cblk[col] ^ zi.q) != rb) continue;
-          TAcc x = (TAcc)cr[zi.cpos[col]];
-          const TAcc* ur = us + (a + b * d.chi) * ld;
-          URow<TAcc, NN>::fma_row(x, ur, part);
+        if (hoist) {
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            if (b >= d.chi) break;
+            if ((int)(cpk[b] >> 31) != rb) continue;
+            TAcc x = (TAcc)cr[cpk[b] & 0x7fffffffu];
+            URow<TAcc, NN>::fma_row(x, us + (a + b * d.chi) * ld, part);
+          }
+        } else {
+          for (int b = 0; b < d.chi; ++b) {
+            const long long col = col0 + b * d.kb_stride;
+            if ((zi.cblk[col] ^ zi.q) != rb) continue;
+            TAcc x = (TAcc)cr[zi.cpos[col]];
+            const TAcc* ur = us + (a + b * d.chi) * ld;
+            URow<TAcc, NN>::fma_row(x, ur, part);
+          }
         }
 #pragma unroll
         for (int n = 0; n < NN; ++n) acc[n] += part[n];
