@@ -20,7 +20,7 @@ paper's order and notation:
   * Y matrix, trace and Gu-Wen ratio X ................................... Sec. 4.1.2, Eqs. (ratio_X), (Matrix_Y); Sec. 4.2.11
   * ln Z^(p) = K^(p) + ln Tr T^(p), K recurrence ......................... Sec. 4.1.1, Eqs. (eq_lnZ), (K_recurrence)
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * Ising: sigma_0 = +1, sigma_1 = -1, W_{s s'} = exp(beta s s'), V_s = exp(beta h s).
   * hat copy = the copy whose Current leg c stays open; combined index
     (hat, check) = hat + check * chi_j (Sec. 3.2, text after Eq. Contraction_NewTensor).

@@ -24,7 +24,7 @@ def lib_path():
     return build.build()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = _declared()
     for n in ("hotrg_init_ising", "hotrg_step", "hotrg_isometry", "hotrg_free_energy"):
         assert n in names
