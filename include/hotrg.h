@@ -152,9 +152,11 @@ int hotrg_leg_parity(hotrg_ctx* ctx, int* parity, int cap, int* n);
  * ran.  Errors: EINVAL, ESTATE (no step yet). */
 int hotrg_bottleneck_flops(hotrg_ctx* ctx, double* dense, double* performed, int* z2_blocks);
 
-/* Record CUDA events around the phases of every later step (enable = 1) or
- * stop (0).  hotrg_step_times() then returns, after synchronising, the
- * milliseconds of the last step per phase: [0] leg permutation, [1]
+/* Record CUDA events around the phases of every later step (enable = 1), around
+ * the bottleneck GEMM launches only, summed over all steps until the next
+ * hotrg_step_times() call (enable = 2: no per-step read-back needed), or stop
+ * (0).  hotrg_step_times() then returns, after synchronising, the
+ * milliseconds of the last step (enable = 1) per phase: [0] leg permutation, [1]
  * environment Grams and A assembly, [2] Jacobi, [3] choice/truncation,
  * [4] BF16 split of T, [5] prime-side chain, [6] bottleneck GEMM, [7]
  * non-prime chain, [8] trace / normalisation, [9] FP32 warm start of the

@@ -260,8 +260,9 @@ def hotrg_bottleneck_flops(ctx):
     return dense.value, done.value, bool(z2.value)
 
 
-def hotrg_profile(ctx, enable: bool):
-    _check(load().hotrg_profile(ctx, 1 if enable else 0), "hotrg_profile")
+def hotrg_profile(ctx, mode):
+    """0: off; 1 (or True): every phase of each step; 2: bottleneck GEMMs, summed over steps."""
+    _check(load().hotrg_profile(ctx, int(mode)), "hotrg_profile")
 
 
 PHASES = ["permute", "environment", "jacobi", "select", "split", "prime_chain", "bottleneck",

@@ -229,18 +229,21 @@ cudaEvent_t next_event(hotrg_ctx* c) {
 }
 
 // RAII phase mark: records a start/stop event pair on the stream when profiling
+// Events around one part of a step: every part (profile 1), or the bottleneck GEMM
+// launches only (profile 2, phase 6), kept across steps until hotrg_step_times reads them
 struct Phase {
   hotrg_ctx* c;
   int id;
+  bool on;
   cudaEvent_t e0 = nullptr;
-  Phase(hotrg_ctx* c_, int id_) : c(c_), id(id_) {
-    if (c->profile) {
+  Phase(hotrg_ctx* c_, int id_) : c(c_), id(id_), on(c_->profile == 1 || (c_->profile == 2 && id_ == 6)) {
+    if (on) {
       e0 = next_event(c);
       cudaEventRecord(e0, c->stream);
     }
   }
   ~Phase() {
-    if (c->profile) {
+    if (on) {
       cudaEvent_t e1 = next_event(c);
       cudaEventRecord(e1, c->stream);
       c->marks.push_back({id, {e0, e1}});
@@ -625,8 +628,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below;
   c->last_fp64 = fp64 ? 1 : 0;
 
-  c->marks.clear();
-  c->event_next = 0;
+  if (c->profile != 2) {   // profile 2 keeps the marks of several steps
+    c->marks.clear();
+    c->event_next = 0;
+  }
   CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * RR));
   CHECK_ALLOC(dev_alloc(c, c->Xp, sizeof(double) * RR));
   bool same = true;
@@ -1799,8 +1804,10 @@ int hotrg_set_slice_budget(hotrg_ctx* c, double bytes) {
 }
 
 int hotrg_profile(hotrg_ctx* c, int enable) {
-  if (!c) return HOTRG_EINVAL;
-  c->profile = enable ? 1 : 0;
+  if (!c || enable < 0 || enable > 2) return HOTRG_EINVAL;
+  c->profile = enable;
+  c->marks.clear();
+  c->event_next = 0;
   return HOTRG_OK;
 }
 
@@ -1817,6 +1824,10 @@ int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int*
     if (cudaEventElapsedTime(&t, m.second.first, m.second.second) != cudaSuccess) return cuda_status(c);
     ms[m.first] += t;
     if (launches) launches[m.first] += 1;
+  }
+  if (c->profile == 2) {   // read once: start the next collection
+    c->marks.clear();
+    c->event_next = 0;
   }
   if (n) *n = 12;
   if (contraction_fp64) *contraction_fp64 = c->last_fp64;
