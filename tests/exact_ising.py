@@ -96,3 +96,28 @@ def lattice_after(d: int, axes) -> tuple:
     for a in axes:
         ext[a] *= 2
     return tuple(ext)
+
+
+def brute_force_energy(shape: tuple, beta: float, h: float) -> float:
+    """u = -d(ln Z / N)/d beta = <H> / N of the periodic lattice `shape`, by enumeration."""
+    n = int(np.prod(shape))
+    if n > 24:
+        raise ValueError("lattice too large for brute force")
+    states = np.array(list(itertools.product([1.0, -1.0], repeat=n))).reshape((-1,) + tuple(shape))
+    bonds = np.zeros(states.shape[0])
+    for k in range(len(shape)):
+        bonds += (states * np.roll(states, -1, axis=1 + k)).reshape(states.shape[0], -1).sum(1)
+    mag = states.reshape(states.shape[0], -1).sum(1)
+    expo = beta * bonds + beta * h * mag
+    w = np.exp(expo - expo.max())
+    return float(-(w * (bonds + h * mag)).sum() / w.sum() / n)
+
+
+def onsager_energy_per_site(beta: float) -> float:
+    """Onsager: u = -coth(2b) [1 + (2/pi) (2 tanh^2 2b - 1) K(k)], k = 2 sinh 2b / cosh^2 2b,
+    K the complete elliptic integral of the first kind (infinite square lattice, h = 0)."""
+    from scipy import special
+
+    k = 2.0 * math.sinh(2 * beta) / math.cosh(2 * beta) ** 2
+    kk = special.ellipk(k * k)
+    return -(1.0 / math.tanh(2 * beta)) * (1.0 + (2.0 / math.pi) * (2.0 * math.tanh(2 * beta) ** 2 - 1.0) * kk)
