@@ -24,7 +24,9 @@ first-order results, written out here):
     the same isometry, so it leaves ln Z unchanged and is left out.
   * pairs (k kept, l discarded) with |lambda_k - lambda_l| <= 1e-12 lambda_1
     have no derivative (the truncation is not differentiable there); their terms
-    are left out and counted.
+    are left out, and counted when their coupling |v_l . dA u_k| exceeds
+    1e-9 lambda_1 (a pair kept apart by a symmetry of dA, such as opposite Z2
+    parity, has zero coupling and is harmless).
   * the choice between U and U' (epsilon vs epsilon') and the sign gauge are
     locally constant in beta and contribute nothing.
   * beta > 0: dX_{s1}/d beta = sigma cosh / (2 sqrt(sinh)) is infinite at beta = 0.
@@ -115,7 +117,8 @@ def kept_eigenvector_dot(lam: np.ndarray, v: np.ndarray, chi_new: int, da: np.nd
         for l in range(chi_new, n):
             gap = lam[k] - lam[l]
             if abs(gap) <= tol:
-                skipped += 1
+                if abs(z[l, k]) > 1e-9 * lam[0]:
+                    skipped += 1
                 continue
             du[:, k] += v[:, l] * (z[l, k] / gap)
     return du, skipped
