@@ -58,7 +58,14 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
   const int nw = (int)(gthreads >> 5);
   const int ntasks = nmat * npairs;
   // the computed inner product carries rounding of order n eps sqrt(a b): a
-  // tolerance below that level would keep rotating rounding noise forever
+  // tolerance below that level would keep rotating rounding noise forever.  A pair
+  // is rotated only if |g| > tol max(a, b), not tol sqrt(a b): the rotation it would
+  // apply to V is g / (a - b), below tol either way, but a column at rounding level
+  // (a near-null direction of A) carries noise of order eps times the large column it
+  // was last rotated against, and the relative test would rotate that pair forever.
+  // Columns with a squared norm below 1e-280 are left alone: their squares and products
+  // are subnormal, tol max(a, b) underflows to 0, and any nonzero g would rotate them
+  // forever (the environments of a trace-normalised tensor have lambda_1 >> 1e-140)
   const double tol = 4.0 * (double)n * 2.220446049250313e-16;
 
   int sweep = 1;
@@ -91,7 +98,8 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
           b += __shfl_xor_sync(0xffffffffu, b, o);
           g += __shfl_xor_sync(0xffffffffu, g, o);
         }
-        bool rot = (g != 0.0) && (fabs(g) > tol * sqrt(a * b));
+        const double big = fmax(a, b);
+        bool rot = (g != 0.0) && big > 1e-280 && (fabs(g) > tol * big);
         if (!rot) continue;
         double zeta = (b - a) / (2.0 * g);
         double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
                                                      const double* __restrict__ V, int n,
                                                      int leg_index, int nnew, double* lam_sorted,
                                                      double* U64, float* U32, LegResult* res,
-                                                     const int* sweeps) {
+                                                     const int* sweeps, int* rank_out) {
   extern __shared__ double sm[];
   double* lam = sm;                         // [2][n]
   int* piv = (int*)(lam + 2 * n);           // [2][n]
@@ -451,6 +459,8 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
     lam_sorted[e] = lam[side * n + order[side * n + r]];
   }
   const int side = s_choice;
+  if (rank_out)   // rank of every eigenvector of the chosen side in the sorted order
+    for (int r = threadIdx.x; r < n; r += blockDim.x) rank_out[order[side * n + r]] = r;
   const double* Vm = V + (long long)(2 * leg_index + side) * nn;
   for (int e = threadIdx.x; e < n * nnew; e += blockDim.x) {
     int row = e / nnew, col = e % nnew;
@@ -463,11 +473,11 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
 
 void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
                    double* lam_sorted, double* U64, float* U32, LegResult* res,
-                   const int* sweeps, cudaStream_t s) {
+                   const int* sweeps, cudaStream_t s, int* rank_out) {
   size_t smem = (size_t)2 * n * sizeof(double) + (size_t)6 * n * sizeof(int);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  select_kernel<<<1, 512, smem, s>>>(W, V, n, leg_index, nnew, lam_sorted, U64, U32, res, sweeps);
+  select_kernel<<<1, 512, smem, s>>>(W, V, n, leg_index, nnew, lam_sorted, U64, U32, res, sweeps, rank_out);
   ++g_launches;
 }
 
