@@ -52,6 +52,11 @@ WORKLOADS = {
     "batch3d_mixed": dict(d=3, chi=12, beta=0.22, h=0.0, first=2, growth=3,
                           text="batching form: 64 independent 3D Ising HOTRG instances, chi in "
                                "{6,8,10,12} x 16, beta uniform in [0.20,0.24], h in {0,0.01}, axes z,x,y"),
+    # differentiation form: d/d beta carried through every step (FP64 dense form), the
+    # internal energy per site; checked against central differences of FP64 runs
+    "energy3d_chi12": dict(d=3, chi=12, beta=0.22, h=0.0, first=2, growth=3,
+                           text="differentiation form: 3D Ising HOTRG d=3 chi=12 beta=0.22 h=0 with "
+                                "d/d beta in forward mode (internal energy), axes z,x,y"),
 }
 
 
@@ -397,6 +402,121 @@ def batch_arm(args):
     return 0
 
 
+def energy_arm(args):
+    """Differentiation form: 3D Ising chi = 12 steps that carry d/d beta (FP64 dense form)
+    and end with the internal energy per site; the energy is checked against central
+    differences (beta +- 1e-5) of two FP64 runs over the same steps.  Metric: steps/s with
+    the derivative carried."""
+    import torch
+
+    import paper_2110_03607_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
+    g = pkg.Hotrg(D, BETA, H, precision=pkg.PREC_FP64)
+    pkg.hotrg_set_tangent(g.ctx, True)
+    for a in axes[: GROWTH_STEPS + args.warmup]:
+        g.step(a, CHI)
+    pkg.hotrg_profile(g.ctx, 2)
+    timed_axes = axes[GROWTH_STEPS + args.warmup:]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    bn_done = 0.0
+    launches0 = pkg.hotrg_launch_count(g.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for a in timed_axes:
+        g.step(a, CHI)
+        bn_done += pkg.hotrg_bottleneck_flops(g.ctx)[1]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = pkg.hotrg_launch_count(g.ctx) - launches0
+    sampler.stop()
+    clocks = sampler.summary()
+    gemm_ms, gemm_n, _ = pkg.hotrg_step_times(g.ctx)
+    dlnz, energy, degenerate = g.energy()
+    lnz = g.free_energy()[0]
+    g.close()
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
+    K = len(timed_axes)
+    value = whole_job_rate(K, world, elapsed_ms)
+
+    # central differences of FP64 runs over the same steps (untimed), beta +- 1e-5 and 1e-4
+    def ln_z_at(b):
+        f = pkg.Hotrg(D, b, H, precision=pkg.PREC_FP64)
+        for a in axes:
+            f.step(a, CHI)
+        v = f.free_energy()[0]
+        f.close()
+        return v
+
+    fds = {db: (ln_z_at(BETA + db) - ln_z_at(BETA - db)) / (2 * db) for db in (1e-5, 1e-4)}
+    fd = fds[1e-5]
+
+    # roofline of the bottleneck region: per c'-slice one FP64 GEMM for C and two for
+    # dC = T^ . dB^T + dT^ . B^T, each 2 R^2 Nc flops
+    n_regions = gemm_n["bottleneck"]
+    region_ms = gemm_ms["bottleneck"] / max(1, n_regions)
+    flops_per_region = 3.0 * bn_done / max(1, n_regions)
+    achieved = flops_per_region / (region_ms / 1000.0) / 1e12 if region_ms > 0 else None
+    if rank == 0:
+        line = {
+            "metric": "3D-Ising chi=12 HOTRG steps/s carrying d/d beta (internal energy), FP64",
+            "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Ising initial tensor and its beta-derivative from beta, h; no dataset)",
+            "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
+                                   f"{args.warmup} warm-up steps, steps {GROWTH_STEPS + args.warmup + 1}-"
+                                   f"{GROWTH_STEPS + args.warmup + K} timed",
+                       "precision": "fp64", "z2_blocks": False,
+                       "l2": "inputs larger than L2 (per-slice operands and their derivatives)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "ln_z_per_site": lnz,
+            "dlnz_dbeta_per_site": dlnz,
+            "energy_per_site": energy,
+            "energy_central_difference": -fd,
+            "rel_err_energy_vs_central_difference": abs(dlnz - fd) / abs(fd),
+            "rel_err_energy_vs_central_difference_by_step": {str(k): abs(dlnz - v) / abs(v)
+                                                              for k, v in fds.items()},
+            # the central difference errs by c db^2: one Richardson step removes that term
+            "rel_err_energy_vs_richardson_extrapolated_difference":
+                abs(dlnz - (fds[1e-5] - (fds[1e-4] - fds[1e-5]) / 99.0)) / abs(fd),
+            "degenerate_pairs": degenerate,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                         "frac": achieved / 1.25 if achieved else None, "traffic": None,
+                         "peak_source": "nominal GB300 FP64 (no measured FP64 peak)",
+                         "note": "bottleneck region per c'-slice: three FP64 GEMMs of 2 R^2 Nc flops "
+                                 "(C, T^.dB^T, dT^.B^T) and one vector add"},
+            "e2e": None,
+            "e2e_note": "inputs are beta and h only (the tensors are built on the device); "
+                        "the end-to-end contract of the default workload does not apply",
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,6 +539,8 @@ def main():
         return reference_arm(args)
     if args.workload == "batch3d_mixed":
         return batch_arm(args)
+    if args.workload == "energy3d_chi12":
+        return energy_arm(args)
 
     import torch
 

@@ -190,6 +190,41 @@ int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
 int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
                      int* status);
 
+/* Differentiation form: carry dT = dT/d beta through every later step in
+ * forward mode, so that hotrg_energy() returns d(ln Z/V)/d beta and the
+ * internal energy u = -d(ln Z/V)/d beta of the HOTRG approximation (Sec. 2
+ * model; the paper does not differentiate the method).  Per step: the
+ * derivatives of the chosen environments, dS = dX X^T + X dX^T and dA =
+ * sum dS^ S~ + S^ dS~ (Sec. 3.2, Sec. 4.2.4); of the kept eigenvectors,
+ * du_k = sum over discarded l of v_l (v_l . dA u_k) / (lambda_k - lambda_l)
+ * (Sec. 4.2.5; rotations inside the kept space are a change of basis on a
+ * bond whose two ends share the isometry, so ln Z does not depend on them);
+ * of the new tensor by the product rule over its two copies of T and its
+ * 2(d-1) isometries (Sec. 4.2.9); and of the trace bookkeeping (Secs. 4.1.1,
+ * 4.2.16).  Pairs with |lambda_k - lambda_l| <= 1e-12 lambda_1 across the
+ * cut have no derivative: their terms are left out, and counted when their
+ * coupling |v_l . dA u_k| exceeds 1e-9 lambda_1.  While on, the contraction
+ * runs densely in FP64 (not in split BF16, not in Z2 blocks; the Grams and
+ * the eigen-solver keep the block form of hotrg_set_z2, whose eigenvectors
+ * have exact parities) and a step costs about three times a forward FP64
+ * step; hotrg_step waits once per step for the isometry choice.
+ * enable = 1 needs a context from hotrg_init_ising with beta > 0 and no step
+ * yet (dT^(0) is the beta-derivative of Eq. 2.4); enable = 0 stops carrying
+ * it.  hotrg_set_tensor turns it off.  Errors: EINVAL (not an Ising context,
+ * beta = 0, steps already taken), ENOMEM, ECUDA, ESTATE. */
+int hotrg_set_tangent(hotrg_ctx* ctx, int enable);
+
+/* After synchronising: *dlnz_dbeta = d(ln Z^(p) / 2^p)/d beta of the last
+ * step (of T^(0) before any step), *energy = its negative (the internal
+ * energy per site, bond and field terms), *degenerate_pairs = eigen pairs
+ * left out so far (see hotrg_set_tangent).  Any out-pointer may be NULL.
+ * Errors: EINVAL, ESTATE (derivative not carried), a recorded device failure. */
+int hotrg_energy(hotrg_ctx* ctx, double* dlnz_dbeta, double* energy, int* degenerate_pairs);
+
+/* dT/d beta of the current normalised tensor, d(T / Tr T), in the layout of
+ * hotrg_tensor.  Errors: as hotrg_tensor, and ESTATE if not carried. */
+int hotrg_tangent_tensor(hotrg_ctx* ctx, double* dT, int64_t cap, int dims[8]);
+
 /* The isometry U~ chosen by the last step for lattice axis `leg` (a
  * transverse axis of that step): a rows x cols row-major FP64 matrix, rows
  * = chi_leg^2 indexed by (hat + check * chi_leg) (Sec. 3.2), cols =

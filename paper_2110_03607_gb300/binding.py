@@ -74,6 +74,9 @@ def load():
         "hotrg_set_parity": (I, [P, ctypes.POINTER(I)]),
         "hotrg_leg_parity": (I, [P, ctypes.POINTER(I), I, ctypes.POINTER(I)]),
         "hotrg_bottleneck_flops": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "hotrg_set_tangent": (I, [P, I]),
+        "hotrg_energy": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "hotrg_tangent_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
         "hotrg_profile": (I, [P, I]),
         "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -260,6 +263,31 @@ def hotrg_bottleneck_flops(ctx):
     return dense.value, done.value, bool(z2.value)
 
 
+def hotrg_set_tangent(ctx, enable: bool = True):
+    """Carry dT/d beta through the later steps (Ising context, before the first step)."""
+    _check(load().hotrg_set_tangent(ctx, 1 if enable else 0), "hotrg_set_tangent")
+
+
+def hotrg_energy(ctx):
+    """(d(ln Z/V)/d beta, internal energy per site, degenerate pairs left out) of the last step."""
+    g, u, deg = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().hotrg_energy(ctx, ctypes.byref(g), ctypes.byref(u), ctypes.byref(deg)), "hotrg_energy")
+    return g.value, u.value, deg.value
+
+
+def hotrg_tangent_tensor(ctx, out=None):
+    """d(T / Tr T)/d beta of the current tensor in the layout of hotrg_tensor."""
+    dims = (ctypes.c_int * 8)()
+    lib = load()
+    lib.hotrg_tangent_tensor(ctx, None, 0, dims)
+    shape = [x for x in dims if x > 0]
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    n = int(np.prod(shape))
+    _check(lib.hotrg_tangent_tensor(ctx, _ptr(out), n, dims), "hotrg_tangent_tensor")
+    return out
+
+
 def hotrg_profile(ctx, mode):
     """0: off; 1 (or True): every phase of each step; 2: bottleneck GEMMs, summed over steps."""
     _check(load().hotrg_profile(ctx, int(mode)), "hotrg_profile")
@@ -336,6 +364,9 @@ class Hotrg:
 
     def free_energy(self):
         return hotrg_free_energy(self.ctx)
+
+    def energy(self):
+        return hotrg_energy(self.ctx)
 
     def close(self):
         if self.ctx:

@@ -14,7 +14,8 @@ LIB = os.path.join(PKG, "libhotrg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 SOURCES = ["hotrg_api.cu", "kernels_tensor.cu", "kernels_env.cu", "kernels_eig.cu",
-           "kernels_chain.cu", "kernels_tc_gemm.cu", "kernels_z2.cu", "hotrg_noalloc.cu"]
+           "kernels_chain.cu", "kernels_tc_gemm.cu", "kernels_z2.cu", "kernels_tangent.cu",
+           "hotrg_noalloc.cu"]
 
 
 def _nvcc() -> str:

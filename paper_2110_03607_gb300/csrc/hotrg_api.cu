@@ -180,6 +180,13 @@ struct hotrg_ctx {
   Buf T, T2, Xp, parts, S, Amat, W, V, lam, U64, U32, legres, Y, state, counters, sweeps;
   Buf Ap, Bp, Cb, chA, chB;
   Buf J32, Gns, Vtmp;   // eigen-solver warm start
+  // d/d beta carried with T in forward mode (Ising runs; FP64 dense form while on):
+  // dT in the slot layout of T, its trace bookkeeping in tstate
+  int tangent = 0;
+  int is_ising = 0;
+  double h = 0.0;
+  Buf dT, dT2, dTb, dXp, dS, dA, dU64, eG, eZ, eZt, rank, Yd, tstate;
+  Buf dchA, dchB, dchT, dBp, tBp, dCb, tCb;
 };
 
 namespace {
@@ -425,6 +432,21 @@ void trace_and_normalise(hotrg_ctx* c, double* Tsrc, int first) {
   launch_scale(Tsrc, (double*)c->T.p, tensor_elems(c), st, c->stream);
 }
 
+// The same for the derivative dTsrc of the new, unnormalised tensor, after
+// trace_and_normalise has run: d ln Tr, the d/d beta of the ln Z bookkeeping, and
+// c->dT = d(T / Tr T) = dTsrc / Tr T - (d ln Tr) c->T.
+void tangent_trace_and_normalise(hotrg_ctx* c, const double* dTsrc, int first) {
+  int d = c->d;
+  int chi_c = c->chis[c->order[0]];
+  long long pn = 1;
+  for (int s = 1; s < d; ++s) pn *= c->chis[c->order[s]];
+  const DevState* st = (const DevState*)c->state.p;
+  TanState* tst = (TanState*)c->tstate.p;
+  launch_trace_y(dTsrc, chi_c, pn, (double*)c->Yd.p, c->stream);
+  launch_finish_tangent((const double*)c->Yd.p, chi_c, st, tst, c->p, first, c->stream);
+  launch_tangent_scale(dTsrc, (const double*)c->T.p, (double*)c->dT.p, tensor_elems(c), st, tst, c->stream);
+}
+
 int start_run(hotrg_ctx* c) {
   CHECK_ALLOC(dev_alloc(c, c->state, sizeof(DevState)));
   CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
@@ -479,6 +501,8 @@ int hotrg_init_ising(int d, double beta, double h, hotrg_ctx** out) {
   hotrg_ctx* c = new hotrg_ctx();
   c->d = d;
   c->beta = beta;
+  c->h = h;
+  c->is_ising = 1;
   for (int k = 0; k < d; ++k) {
     c->chis[k] = 2;
     c->order[k] = k;
@@ -547,6 +571,7 @@ int hotrg_set_tensor(hotrg_ctx* c, const int* chis, const double* T) {
   interchange_to_slots(c, (const double*)c->Xp.p, (double*)c->T.p);
   c->last_valid = 0;
   c->z2_valid = 0;   // until hotrg_set_parity declares and checks the parities
+  c->tangent = 0;    // the derivative of a tensor set from outside is not known
   int r = cuda_status(c);
   if (r != HOTRG_OK) return r;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
@@ -563,28 +588,33 @@ int hotrg_set_stream(hotrg_ctx* c, void* stream) {
 int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_fn, void* user) {
   if (!c || (!alloc) != (!free_fn)) return HOTRG_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
-  // keep the tensor and the run state, drop every workspace
-  Buf keep[2] = {c->T, c->state};
-  size_t keep_bytes[2] = {c->T.bytes, c->state.bytes};
-  std::vector<char> host[2];
-  for (int i = 0; i < 2; ++i) {
+  // keep the tensor and the run state (and their derivatives), drop every workspace
+  Buf keep[4] = {c->T, c->state, c->dT, c->tstate};
+  size_t keep_bytes[4] = {c->T.bytes, c->state.bytes, c->tangent ? c->dT.bytes : 0,
+                          c->tangent ? c->tstate.bytes : 0};
+  std::vector<char> host[4];
+  for (int i = 0; i < 4; ++i) {
     host[i].resize(keep_bytes[i]);
-    if (keep[i].p && cudaMemcpy(host[i].data(), keep[i].p, keep_bytes[i], cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (keep_bytes[i] && keep[i].p &&
+        cudaMemcpy(host[i].data(), keep[i].p, keep_bytes[i], cudaMemcpyDeviceToHost) != cudaSuccess)
       return cuda_status(c);
   }
   int n = 0;
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
+              &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
+              &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
+              &c->tCb};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
   c->ffn = free_fn;
   c->user = user;
   c->last_valid = 0;
-  Buf* kb[2] = {&c->T, &c->state};
-  for (int i = 0; i < 2; ++i) {
+  Buf* kb[4] = {&c->T, &c->state, &c->dT, &c->tstate};
+  for (int i = 0; i < 4; ++i) {
     if (!keep_bytes[i]) continue;
     CHECK_ALLOC(dev_alloc(c, *kb[i], keep_bytes[i]));
     if (cudaMemcpy(kb[i]->p, host[i].data(), keep_bytes[i], cudaMemcpyHostToDevice) != cudaSuccess)
@@ -625,7 +655,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const long long RR = R * R;
   // bottleneck work of this step: 2 * R^2 * (P_new P) per c'-slice, chi_c slices
   const double bn_flops = 2.0 * (double)R * (double)R * (double)Pn * (double)P * (double)chi_c;
-  const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below;
+  // the derivative d/d beta, when carried, runs with the FP64 dense form
+  const bool tangent = c->tangent != 0;
+  const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below || tangent;
   c->last_fp64 = fp64 ? 1 : 0;
 
   if (c->profile != 2) {   // profile 2 keeps the marks of several steps
@@ -641,6 +673,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     Phase ph(c, 0);
     permute_slots(c, (const double*)c->T.p, c->order, (double*)c->T2.p, to, 1.0);
     std::swap(c->T, c->T2);
+    if (tangent) {
+      CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * RR));
+      permute_slots(c, (const double*)c->dT.p, c->order, (double*)c->dT2.p, to, 1.0);
+      std::swap(c->dT, c->dT2);
+    }
     Tc = (double*)c->T.p;
     for (int k = 0; k < d; ++k) c->order[k] = to[k];
   }
@@ -1057,6 +1094,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   CHECK_ALLOC(dev_alloc(c, c->U64, sizeof(double) * u_total));
   CHECK_ALLOC(dev_alloc(c, c->U32, sizeof(float) * u_total));
   CHECK_ALLOC(dev_alloc(c, c->legres, sizeof(LegResult) * kMaxD));
+  long long rank_off[kMaxD], rank_total = 0;
+  for (int j = 1; j < d; ++j) {
+    rank_off[j] = rank_total;
+    rank_total += (long long)chij[j] * chij[j];
+  }
+  if (tangent) CHECK_ALLOC(dev_alloc(c, c->rank, sizeof(int) * rank_total));
   for (int j = 1; j < d; ++j) {
     Phase ph(c, 3);
     int n = chij[j] * chij[j];
@@ -1064,7 +1107,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     launch_select((const double*)c->W.p + mat_elem_off[2 * j], (const double*)c->V.p + mat_elem_off[2 * j],
                   n, 0, nnew[j], (double*)c->lam.p + lam_off[j], (double*)c->U64.p + u_off[j],
                   (float*)c->U32.p + u_off[j], (LegResult*)c->legres.p + j,
-                  (int*)c->sweeps.p + mat_of_leg[j], s);
+                  (int*)c->sweeps.p + mat_of_leg[j], s, tangent ? (int*)c->rank.p + rank_off[j] : nullptr);
   }
 
   if (pending_error(c, "the selection") != HOTRG_OK) return HOTRG_ECUDA;
@@ -1102,13 +1145,69 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     }
     if (pure) {
       track = true;
-      z2 = c->z2_enabled != 0;
+      z2 = c->z2_enabled != 0 && !tangent;
     } else {
       c->z2_valid = 0;
     }
   }
 
   if (pending_error(c, "the parity read-back") != HOTRG_OK) return HOTRG_ECUDA;
+  // ---- d/d beta of the chosen environments and of the kept eigenvectors
+  // dS = dX X^T + X dX^T (Sec. 3.2), dA = sum dS^ S~ + S^ dS~ (Sec. 4.2.4), and
+  // du_k = sum_{l discarded} v_l (v_l . dA u_k) / (lam_k - lam_l) (Sec. 4.2.5)
+  if (tangent) {
+    Phase ph(c, 1);
+    LegResult hres[kMaxD];
+    if (cudaMemcpyAsync(hres, c->legres.p, sizeof(LegResult) * kMaxD, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    long long eig_max = 1;
+    for (int j = 1; j < d; ++j) eig_max = std::max<long long>(eig_max, (long long)chij[j] * chij[j] * nnew[j]);
+    CHECK_ALLOC(dev_alloc(c, c->dXp, sizeof(double) * RR));
+    CHECK_ALLOC(dev_alloc(c, c->dS, sizeof(double) * 4 * nlegs * mmax * mmax));
+    CHECK_ALLOC(dev_alloc(c, c->dA, sizeof(double) * total_mat_elems));
+    CHECK_ALLOC(dev_alloc(c, c->dU64, sizeof(double) * u_total));
+    CHECK_ALLOC(dev_alloc(c, c->eG, sizeof(double) * eig_max));
+    CHECK_ALLOC(dev_alloc(c, c->eZ, sizeof(double) * eig_max));
+    CHECK_ALLOC(dev_alloc(c, c->eZt, sizeof(double) * eig_max));
+    TanState* tst = (TanState*)c->tstate.p;
+    for (int j = 1; j < d; ++j) {
+      const long long m = (long long)chij[j] * chi_c;
+      const long long K = RR / m;
+      const int side = hres[j].chose_prime;   // 0: A^(j), 1: A'^(j)
+      double* dS0 = (double*)c->dS.p + ((long long)(j - 1) * 4) * mmax * mmax;
+      for (int kind = 2 * side; kind < 2 * side + 2; ++kind) {
+        long long size[kMaxDims], ist[kMaxDims];
+        int pslot[kMaxDims];
+        const int nd = gram_dims(j, kind, size, ist, pslot);
+        launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
+        launch_permute((const double*)c->dT.p, (double*)c->dXp.p, nd, size, ist, 1.0, s);
+        const int nsplit = gram_splits(m, K);
+        launch_gemm_nt_f64((const double*)c->dXp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p, m, m * m,
+                           (int)m, (int)m, K, nsplit, 0, s);
+        long long kchunk = (K + nsplit - 1) / nsplit;
+        kchunk = (kchunk + 15) / 16 * 16;
+        const int used = (int)((K + kchunk - 1) / kchunk);
+        launch_sym_sum((const double*)c->parts.p, used, (int)m, dS0 + kind * mmax * mmax, s);
+      }
+      const double* S0 = (const double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
+      const long long k0 = 2 * side;
+      double* dAs = (double*)c->dA.p + mat_elem_off[2 * j + side];
+      launch_assemble_dot(S0 + k0 * mmax * mmax, dS0 + k0 * mmax * mmax, S0 + (k0 + 1) * mmax * mmax,
+                          dS0 + (k0 + 1) * mmax * mmax, chij[j], chi_c, dAs, s);
+      const int n = chij[j] * chij[j], nn = nnew[j];
+      const double* Vs = (const double*)c->V.p + mat_elem_off[2 * j + side];   // rows: eigenvectors
+      double* G = (double*)c->eG.p;
+      launch_gemm_nn_f64(dAs, n, (const double*)c->U64.p + u_off[j], nn, G, nn, n, nn, n, 1, 0, 0, 0, s);
+      launch_gemm_nn_f64(Vs, n, G, nn, (double*)c->eZ.p, nn, n, nn, n, 1, 0, 0, 0, s);    // v_i . dA u_k
+      launch_eig_dscale((const double*)c->eZ.p, (const double*)c->lam.p + lam_off[j] + (long long)side * n,
+                        (const int*)c->rank.p + rank_off[j], n, nn, (double*)c->eZt.p, tst, s);
+      launch_gemm_nn_f64((const double*)c->eZt.p, n, Vs, n, G, n, nn, n, n, 1, 0, 0, 0, s);   // dU^T
+      launch_transpose(G, nn, n, (double*)c->dU64.p + u_off[j], s);
+    }
+    if (pending_error(c, "the derivative of the isometries") != HOTRG_OK) return HOTRG_ECUDA;
+  }
   // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
   const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
   const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
@@ -1135,11 +1234,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const int nnew1 = nnew[1];
   int n1_chunk = nnew1;
   {
-    // the Z2 blocks of B and C hold about half of B and C again
+    // the Z2 blocks of B and C hold about half of B and C again; the derivative
+    // adds two more of B and C and three more chain buffers
     const double per_unit =
-        (z2 ? 1.6 : 1.0) * (double)(Ns / nnew1) *
+        (z2 ? 1.6 : 1.0) * (tangent ? 3.0 : 1.0) * (double)(Ns / nnew1) *
             ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
-        2.0 * (double)elt * (double)chain_max / nnew1;
+        (tangent ? 5.0 : 2.0) * (double)elt * (double)chain_max / nnew1;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     double budget = std::min(0.6 * (double)free_b + (double)(c->Bp.bytes + c->Cb.bytes + c->chA.bytes +
@@ -1151,6 +1251,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const long long chain_sub = (chain_max / nnew1) * n1_chunk;
   CHECK_ALLOC(dev_alloc(c, c->chA, elt * chain_sub));
   CHECK_ALLOC(dev_alloc(c, c->chB, elt * chain_sub));
+  if (tangent) {
+    CHECK_ALLOC(dev_alloc(c, c->dchA, elt * chain_sub));
+    CHECK_ALLOC(dev_alloc(c, c->dchB, elt * chain_sub));
+    CHECK_ALLOC(dev_alloc(c, c->dchT, elt * chain_sub));
+  }
   // Z2 index maps.  Rows of T and the contracted index (rho, n^') run over the same
   // slots with the same parities, so one list per parity b serves as the row map
   // (first R_b entries) and, padded with -1 to Kp_b, as the K map of block b.
@@ -1245,6 +1350,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   if (fp64) {
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(double) * Nsub * R));
     CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(double) * R * Nsub));
+    if (tangent) {
+      CHECK_ALLOC(dev_alloc(c, c->dBp, sizeof(double) * Nsub * R));
+      CHECK_ALLOC(dev_alloc(c, c->tBp, sizeof(double) * Nsub * R));
+      CHECK_ALLOC(dev_alloc(c, c->dCb, sizeof(double) * R * Nsub));
+      CHECK_ALLOC(dev_alloc(c, c->tCb, sizeof(double) * R * Nsub));
+    }
     if (z2) {
       CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(double) * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
       CHECK_ALLOC(dev_alloc(c, c->Zb, sizeof(double) * maxL * (Kpb[0] + Kpb[1])));
@@ -1281,6 +1392,21 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const int zchunk = std::max(1, tc_chunk_kblocks() / 2);
   CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
   double* Tn = (double*)c->T2.p;
+  // derivative of the new tensor: the terms through dU^(1) of the last non-prime
+  // stage land in dTn2 and are added at the end
+  double* dTn = nullptr;
+  double* dTn2 = nullptr;
+  if (tangent) {
+    CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * Rn * Rn));
+    CHECK_ALLOC(dev_alloc(c, c->dTb, sizeof(double) * Rn * Rn));
+    dTn = (double*)c->dT2.p;
+    dTn2 = (double*)c->dTb.p;
+  }
+  auto view_elems = [](const View& v) {
+    long long n_ = 1;
+    for (auto& x : v) n_ *= x.size;
+    return n_;
+  };
 
   // products of trailing bond sizes
   auto prod_after = [&](const int* arr, int k) {
@@ -1318,6 +1444,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     for (int k = 1; k < d; ++k) in.push_back({I_NC + k, chij[k], rs[k]});
     for (int k = 1; k < d; ++k) in.push_back({I_NCP + k, chij[k], cs[k]});
     const void* src = Tc + (long long)sl * cs[0];
+    const double* dsrc = tangent ? (const double*)c->dT.p + (long long)sl * cs[0] : nullptr;
     int src_f64 = 1;
     for (int j = 1; j < d; ++j) {
       Phase ph(c, 5);
@@ -1349,6 +1476,14 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       void* dst = last ? c->Bp.p : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
         launch_chain_f64(cd, (const double*)src, (const double*)c->U64.p + u_off[j] + ucol, (double*)dst, s);
+        if (tangent) {   // dX_j = stage(dX_{j-1}, U) + stage(X_{j-1}, dU)
+          double* ddst = last ? (double*)c->dBp.p : (double*)((j & 1) ? c->dchA.p : c->dchB.p);
+          double* tdst = last ? (double*)c->tBp.p : (double*)c->dchT.p;
+          launch_chain_f64(cd, dsrc, (const double*)c->U64.p + u_off[j] + ucol, ddst, s);
+          launch_chain_f64(cd, (const double*)src, (const double*)c->dU64.p + u_off[j] + ucol, tdst, s);
+          launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
+          dsrc = ddst;
+        }
       } else if (c->f64_chains) {
         cd.npieces = npieces;
         cd.piece_stride = Nc * Kpad;
@@ -1427,6 +1562,13 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     if (fp64) {
       launch_gemm_nt_f64(Tc, R, (const double*)c->Bp.p, R, (double*)c->Cb.p, Nc, 0, (int)R, (int)Nc,
                          R, 1, 0, s);
+      if (tangent) {   // dC = T^ . dB^T + dT^ . B^T
+        launch_gemm_nt_f64(Tc, R, (const double*)c->dBp.p, R, (double*)c->dCb.p, Nc, 0, (int)R, (int)Nc, R, 1,
+                           0, s);
+        launch_gemm_nt_f64((const double*)c->dT.p, R, (const double*)c->Bp.p, R, (double*)c->tCb.p, Nc, 0,
+                           (int)R, (int)Nc, R, 1, 0, s);
+        launch_axpby(1.0, (const double*)c->tCb.p, 1.0, (double*)c->dCb.p, R * Nc, s);
+      }
     } else {
       if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
                          (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Nc,
@@ -1444,6 +1586,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P});
     for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
     const void* csrc = c->Cb.p;
+    const double* dcsrc = tangent ? (const double*)c->dCb.p : nullptr;
     for (int j = d - 1; j >= 1; --j) {
       Phase ph(c, 7);
       View out;
@@ -1470,6 +1613,15 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                        : ((j & 1) ? c->chA.p : c->chB.p);
       if (fp64) {
         launch_chain_f64(cd, (const double*)csrc, (const double*)c->U64.p + u_off[j], (double*)dst, s);
+        if (tangent) {   // dY_j = stage(dY_{j+1}, U) + stage(Y_{j+1}, dU)
+          const long long slab = (long long)sl * Pn + (long long)n1lo * prod_after(nnew, 1);
+          double* ddst = last ? dTn + slab : (double*)((j & 1) ? c->dchA.p : c->dchB.p);
+          double* tdst = last ? dTn2 + slab : (double*)c->dchT.p;
+          launch_chain_f64(cd, dcsrc, (const double*)c->U64.p + u_off[j], ddst, s);
+          launch_chain_f64(cd, (const double*)csrc, (const double*)c->dU64.p + u_off[j], tdst, s);
+          if (!last) launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
+          dcsrc = ddst;
+        }
       } else if (c->f64_chains) {
         launch_chain_f64acc(cd, csrc, j == d - 1 ? 0 : 1, (const double*)c->U64.p + u_off[j], dst, OUT_F64, s);
       } else if (zfold && j == d - 1) {
@@ -1493,6 +1645,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   }
 
   if (pending_error(c, "the non-prime chain") != HOTRG_OK) return HOTRG_ECUDA;
+  if (tangent) launch_axpby(1.0, dTn2, 1.0, dTn, Rn * Rn, s);
   // ---- bond dims of the new tensor (Sec. 4.2.15 with the axes kept physical)
   for (int j = 1; j < d; ++j) c->chis[to[j]] = nnew[j];
   if (track)
@@ -1506,6 +1659,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   {
     Phase ph(c, 8);
     trace_and_normalise(c, Tn, 0);
+    if (tangent) {
+      CHECK_ALLOC(dev_alloc(c, c->dT, sizeof(double) * Rn * Rn));
+      tangent_trace_and_normalise(c, dTn, 0);
+    }
   }
 
   c->last_valid = 1;
@@ -1791,6 +1948,58 @@ int hotrg_bottleneck_flops(hotrg_ctx* c, double* dense, double* performed, int* 
   return HOTRG_OK;
 }
 
+int hotrg_set_tangent(hotrg_ctx* c, int enable) {
+  if (!c || enable < 0 || enable > 1) return HOTRG_EINVAL;
+  if (!enable) {
+    c->tangent = 0;
+    return HOTRG_OK;
+  }
+  if (c->poisoned) return HOTRG_ESTATE;
+  if (c->tangent) return HOTRG_OK;
+  if (!c->is_ising || c->p != 0 || !(c->beta > 0.0)) return HOTRG_EINVAL;
+  const long long n = tensor_elems(c);
+  CHECK_ALLOC(dev_alloc(c, c->tstate, sizeof(TanState)));
+  CHECK_ALLOC(dev_alloc(c, c->Yd, sizeof(double) * kMaxBond * kMaxBond));
+  CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * n));
+  CHECK_ALLOC(dev_alloc(c, c->dT, sizeof(double) * n));
+  cudaMemsetAsync(c->tstate.p, 0, sizeof(TanState), c->stream);
+  launch_init_ising_dbeta((double*)c->dT2.p, c->d, c->beta, c->h, c->stream);
+  tangent_trace_and_normalise(c, (const double*)c->dT2.p, 1);
+  c->tangent = 1;
+  return cuda_status(c);
+}
+
+int hotrg_energy(hotrg_ctx* c, double* dlnz_dbeta, double* energy, int* degenerate_pairs) {
+  if (!c) return HOTRG_EINVAL;
+  if (!c->tangent) return HOTRG_ESTATE;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  TanState t;
+  if (cudaMemcpy(&t, c->tstate.p, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_status(c);
+  if (dlnz_dbeta) *dlnz_dbeta = t.dln_z_site;
+  if (energy) *energy = -t.dln_z_site;
+  if (degenerate_pairs) *degenerate_pairs = t.degenerate;
+  return HOTRG_OK;
+}
+
+int hotrg_tangent_tensor(hotrg_ctx* c, double* dT, int64_t cap, int dims[8]) {
+  if (!c) return HOTRG_EINVAL;
+  if (!c->tangent) return HOTRG_ESTATE;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  long long n = tensor_elems(c);
+  if (dims)
+    for (int k = 0; k < 8; ++k) dims[k] = k < 2 * c->d ? c->chis[k / 2] : 0;
+  if (!dT || cap < n) return HOTRG_EINVAL;
+  int ra = dev_alloc(c, c->Xp, sizeof(double) * n);
+  if (ra != HOTRG_OK) return ra;
+  slots_to_interchange(c, (const double*)c->dT.p, (double*)c->Xp.p);
+  if (cudaMemcpyAsync(dT, c->Xp.p, sizeof(double) * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+    return cuda_status(c);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
+  return cuda_status(c);
+}
+
 int hotrg_set_fp64_threshold(hotrg_ctx* c, double flops) {
   if (!c || !(flops >= 0.0)) return HOTRG_EINVAL;
   c->fp64_below = flops;
@@ -1853,7 +2062,10 @@ void hotrg_free(hotrg_ctx* c) {
   Buf* b[] = {&c->T,  &c->T2, &c->Xp,     &c->parts, &c->S,     &c->Amat,     &c->W,
               &c->V,  &c->lam, &c->U64,   &c->U32,   &c->legres, &c->Y,       &c->state,
               &c->counters, &c->sweeps, &c->Ap, &c->Bp, &c->Cb, &c->chA, &c->chB,
-              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb};
+              &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
+              &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
+              &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
+              &c->tCb};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);

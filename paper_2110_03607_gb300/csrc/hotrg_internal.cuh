@@ -25,6 +25,16 @@ struct DevState {
   int pad;
 };
 
+// Device-side derivative state of a run (d/d beta, forward mode), beside DevState.
+struct TanState {
+  double dkappa;       // d kappa_p / d beta
+  double dln_tr;       // d ln Tr T^(p) / d beta
+  double dln_z_site;   // d (ln Z^(p) / 2^p) / d beta
+  double dtrace;       // Tr dT^(p)
+  int degenerate;      // eigen pairs across the cut with no derivative (left out)
+  int pad;
+};
+
 // Per-leg results of the isometry selection.
 struct LegResult {
   double eps[2];       // epsilon (A), epsilon' (A')
@@ -91,7 +101,7 @@ void launch_gemm_nt_f64_batched(const double* A, long long lda, const double* B,
                                 long long bsa, long long bsb, long long bsc, cudaStream_t s);
 void launch_select(const double* W, const double* V, int n, int leg_index, int nnew,
                    double* lam_sorted, double* U64, float* U32, LegResult* res,
-                   const int* sweeps, cudaStream_t s);
+                   const int* sweeps, cudaStream_t s, int* rank_out = nullptr);
 
 // ---- kernels_chain.cu
 void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U,
@@ -163,4 +173,18 @@ int tc_gemm_ready();
 int tc_chunk_kblocks();
 
 extern std::atomic<long long> g_launches;   // kernels launched by this library
+// ---- kernels_tangent.cu (d/d beta in forward mode)
+void launch_init_ising_dbeta(double* dT, int d, double beta, double h, cudaStream_t s);
+void launch_sym_sum(const double* parts, int nsplit, int m, double* dS, cudaStream_t s);
+void launch_assemble_dot(const double* sh, const double* dsh, const double* sc, const double* dsc, int chi_j,
+                         int chi_c, double* dA, cudaStream_t s);
+void launch_eig_dscale(const double* Z, const double* lam_sorted, const int* rank, int n, int nnew, double* Zt,
+                       TanState* tst, cudaStream_t s);
+void launch_transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
+void launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+void launch_finish_tangent(const double* Yd, int chi_c, const DevState* st, TanState* tst, int p, int first,
+                           cudaStream_t s);
+void launch_tangent_scale(const double* dT, const double* That, double* out, long long n, const DevState* st,
+                          const TanState* tst, cudaStream_t s);
+
 }  // namespace hotrg

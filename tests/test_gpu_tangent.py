@@ -1,0 +1,158 @@
+"""GPU differentiation form (d/d beta in forward mode) through the C ABI against the
+FP64 tangent oracle, finite differences of the GPU's own FP64 run, exact enumeration
+and Onsager's internal energy."""
+
+import numpy as np
+import pytest
+
+from oracle import hotrg_oracle as o
+from oracle import hotrg_tangent as tg
+from tests import exact_ising as ex
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    import paper_2110_03607_gb300 as p
+
+    assert torch.cuda.is_available()
+    p.load()
+    return p
+
+
+def _gpu_tangent_run(pkg, d, beta, h, chi, axes, z2=True, tensors_at=()):
+    g = pkg.Hotrg(d, beta, h, precision=2, z2=z2)
+    out, tens = [], {}
+    try:
+        pkg.hotrg_set_tangent(g.ctx, True)
+        out.append(g.energy())
+        for i, a in enumerate(axes):
+            g.step(a, chi)
+            lnz, _ = g.free_energy()
+            dlnz, u, deg = g.energy()
+            out.append((dlnz, u, deg, lnz))
+            if i + 1 in tensors_at:
+                tens[i + 1] = (pkg.hotrg_tensor(g.ctx), pkg.hotrg_tangent_tensor(g.ctx))
+    finally:
+        g.close()
+    return out, tens
+
+
+def _gpu_ln_z(pkg, d, beta, h, chi, axes):
+    g = pkg.Hotrg(d, beta, h, precision=0)
+    try:
+        for a in axes:
+            g.step(a, chi)
+        return g.free_energy()[0]
+    finally:
+        g.close()
+
+
+ORACLE_CASES = [
+    (2, 0.35, 0.0, 8, 10),
+    (2, 0.35, 0.0, 12, 12),
+    (3, 0.21, 0.0, 6, 5),
+    (2, 0.5, 0.05, 6, 10),
+    (3, 0.2, 0.0, 4, 6),
+    (3, 0.25, 0.1, 4, 5),
+    (4, 0.15, 0.0, 3, 4),
+]
+
+
+@pytest.mark.parametrize("d,beta,h,chi,nsteps", ORACLE_CASES)
+def test_energy_matches_oracle_every_step(pkg, d, beta, h, chi, nsteps):
+    axes = o.cyclic_axes(d, nsteps)
+    res, _ = _gpu_tangent_run(pkg, d, beta, h, chi, axes)
+    r = tg.HotrgTangentRun(d, beta, h)
+    assert res[0][0] == pytest.approx(r.dln_z, rel=1e-13)
+    for i, a in enumerate(axes):
+        rec = r.step(a, chi)
+        dlnz, u, deg, lnz = res[i + 1]
+        assert deg == rec.degenerate_pairs == 0
+        assert abs(dlnz - rec.dln_z_per_site) <= 1e-10 * abs(rec.dln_z_per_site), (i, dlnz, rec.dln_z_per_site)
+        assert u == -dlnz
+        assert abs(lnz - rec.ln_z_per_site) <= 1e-12 * abs(rec.ln_z_per_site)
+
+
+@pytest.mark.parametrize("d,beta,h,chi,nsteps", [(3, 0.25, 0.1, 4, 4), (2, 0.5, 0.05, 6, 5)])
+def test_tangent_tensor_matches_oracle_elementwise(pkg, d, beta, h, chi, nsteps):
+    axes = o.cyclic_axes(d, nsteps)
+    _, tens = _gpu_tangent_run(pkg, d, beta, h, chi, axes, tensors_at=range(1, nsteps + 1))
+    r = tg.HotrgTangentRun(d, beta, h)
+    for i, a in enumerate(axes):
+        r.step(a, chi)
+        t_gpu, dt_gpu = tens[i + 1]
+        assert t_gpu.shape == r.t.shape and dt_gpu.shape == r.dt.shape
+        np.testing.assert_allclose(t_gpu, r.t, rtol=0, atol=1e-12 * np.abs(r.t).max())
+        np.testing.assert_allclose(dt_gpu, r.dt, rtol=0, atol=1e-10 * np.abs(r.dt).max())
+
+
+def test_z2_setting_does_not_change_the_derivative(pkg):
+    # block-form eigen-solver (z2 on) or dense (off): the same derivative up to rounding
+    axes = o.cyclic_axes(3, 5)
+    a, _ = _gpu_tangent_run(pkg, 3, 0.22, 0.0, 6, axes, z2=True)
+    b, _ = _gpu_tangent_run(pkg, 3, 0.22, 0.0, 6, axes, z2=False)
+    for x, y in zip(a[1:], b[1:]):
+        assert abs(x[0] - y[0]) <= 1e-11 * abs(y[0])
+
+
+# Near beta_c, ln Z of a truncated run is not smooth on the scale of 1e-5 in beta for
+# every chi (2D chi = 16, beta = 0.42: the oracle's own central differences with steps
+# 1e-4, 1e-5, 1e-6 scatter by 1e-3); the cases here are ones where they agree.
+@pytest.mark.parametrize("d,beta,h,chi,nsteps", [(3, 0.22, 0.0, 8, 9), (2, 0.42, 0.0, 12, 16),
+                                                  (4, 0.16, 0.02, 4, 6)])
+def test_energy_matches_central_difference_of_the_gpu_run(pkg, d, beta, h, chi, nsteps):
+    axes = o.cyclic_axes(d, nsteps)
+    res, _ = _gpu_tangent_run(pkg, d, beta, h, chi, axes)
+    db = 1e-5
+    fd = (_gpu_ln_z(pkg, d, beta + db, h, chi, axes) - _gpu_ln_z(pkg, d, beta - db, h, chi, axes)) / (2 * db)
+    dlnz, _, deg, _ = res[-1]
+    assert deg == 0
+    assert abs(dlnz - fd) <= 1e-7 * abs(fd), (dlnz, fd)
+
+
+@pytest.mark.parametrize("d,nsteps,chi,beta,h", [(2, 4, 16, 0.3, 0.1), (3, 3, 16, 0.25, 0.05)])
+def test_untruncated_energy_equals_brute_force(pkg, d, nsteps, chi, beta, h):
+    axes = o.cyclic_axes(d, nsteps, first=d - 1)
+    res, _ = _gpu_tangent_run(pkg, d, beta, h, chi, axes)
+    assert res[0][1] == pytest.approx(ex.brute_force_energy((1,) * d, beta, h), rel=1e-13)
+    for i in range(nsteps):
+        exact = ex.brute_force_energy(ex.lattice_after(d, axes[: i + 1]), beta, h)
+        assert res[i + 1][1] == pytest.approx(exact, rel=1e-11, abs=1e-13), i
+
+
+@pytest.mark.parametrize("beta,chi,gate", [(0.3, 16, 1e-7), (0.5, 16, 1.5e-6), (0.4, 16, 6e-6)])
+def test_energy_against_onsager(pkg, beta, chi, gate):
+    axes = o.cyclic_axes(2, 24)
+    res, _ = _gpu_tangent_run(pkg, 2, beta, 0.0, chi, axes)
+    _, u, deg, _ = res[-1]
+    exact = ex.onsager_energy_per_site(beta)
+    assert abs(u - exact) / abs(exact) <= gate, (u, exact, deg)
+
+
+def test_bad_arguments(pkg):
+    g = pkg.Hotrg(2, 0.3, 0.0)
+    try:
+        with pytest.raises(pkg.HotrgError):
+            g.energy()                          # not carried
+        g.step(0, 4)
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_set_tangent(g.ctx, True)  # steps already taken
+    finally:
+        g.close()
+    g = pkg.Hotrg(2, 0.0, 0.0)
+    try:
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_set_tangent(g.ctx, True)  # beta = 0
+    finally:
+        g.close()
+    t = o.initial_tensor(2, 0.3, 0.0)
+    g = pkg.Hotrg(2, 0.3, tensor=np.ascontiguousarray(t), chis=[2, 2])
+    try:
+        with pytest.raises(pkg.HotrgError):
+            pkg.hotrg_set_tangent(g.ctx, True)  # not an Ising context
+    finally:
+        g.close()
