@@ -57,6 +57,12 @@ WORKLOADS = {
     "energy3d_chi12": dict(d=3, chi=12, beta=0.22, h=0.0, first=2, growth=3,
                            text="differentiation form: 3D Ising HOTRG d=3 chi=12 beta=0.22 h=0 with "
                                 "d/d beta in forward mode (internal energy), axes z,x,y"),
+    # the same over a scan of 32 beta in [0.21, 0.23], stepped together (batching form):
+    # energy and specific heat per site as functions of beta
+    "energy3d_chi12_scan": dict(d=3, chi=12, beta=0.22, h=0.0, first=2, growth=3,
+                                text="differentiation form, beta scan: 32 3D Ising HOTRG instances d=3 "
+                                     "chi=12 h=0, beta uniform in [0.21,0.23], d/d beta in forward mode, "
+                                     "axes z,x,y"),
 }
 
 
@@ -403,10 +409,10 @@ def batch_arm(args):
 
 
 def energy_arm(args):
-    """Differentiation form: 3D Ising chi = 12 steps that carry d/d beta (FP64 dense form)
-    and end with the internal energy per site; the energy is checked against central
-    differences (beta +- 1e-5) of two FP64 runs over the same steps.  Metric: steps/s with
-    the derivative carried."""
+    """Differentiation form: 3D Ising chi = 12 steps that carry d/d beta (dense contraction
+    in the arithmetic of --precision) and end with the internal energy per site; the energy
+    is checked against central differences (beta +- 1e-5, 1e-4) of FP64 runs over the same
+    steps.  Metric: steps/s with the derivative carried."""
     import torch
 
     import paper_2110_03607_gb300 as pkg
@@ -421,7 +427,8 @@ def energy_arm(args):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
-    g = pkg.Hotrg(D, BETA, H, precision=pkg.PREC_FP64)
+    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    g = pkg.Hotrg(D, BETA, H, precision=prec)
     pkg.hotrg_set_tangent(g.ctx, True)
     for a in axes[: GROWTH_STEPS + args.warmup]:
         g.step(a, CHI)
@@ -469,23 +476,40 @@ def energy_arm(args):
     fds = {db: (ln_z_at(BETA + db) - ln_z_at(BETA - db)) / (2 * db) for db in (1e-5, 1e-4)}
     fd = fds[1e-5]
 
-    # roofline of the bottleneck region: per c'-slice one FP64 GEMM for C and two for
-    # dC = T^ . dB^T + dT^ . B^T, each 2 R^2 Nc flops
+    # roofline of the bottleneck region: per c'-slice one GEMM for C and two for
+    # dC = T^ . dB^T + dT^ . B^T, each 2 R^2 Nc flops (algorithmic)
     n_regions = gemm_n["bottleneck"]
     region_ms = gemm_ms["bottleneck"] / max(1, n_regions)
     flops_per_region = 3.0 * bn_done / max(1, n_regions)
     achieved = flops_per_region / (region_ms / 1000.0) / 1e12 if region_ms > 0 else None
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25 if achieved else None, "traffic": None,
+                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+    else:
+        peaks, peak_src = load_peaks()
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        nterms = 6 if args.precision == "bf16x6" else 3
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                "issued_tflops": achieved * nterms if achieved else None,
+                "issued_frac": achieved * nterms / peak if achieved else None}
+    roof["note"] = ("bottleneck region per c'-slice: three GEMMs of 2 R^2 Nc flops "
+                    "(C, T^.dB^T, dT^.B^T) and one vector add")
     if rank == 0:
         line = {
-            "metric": "3D-Ising chi=12 HOTRG steps/s carrying d/d beta (internal energy), FP64",
+            "metric": "3D-Ising chi=12 HOTRG steps/s carrying d/d beta (internal energy)",
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64",
+            "vs_baseline": None,
+            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
+                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ", "fp64": "f64"}[args.precision],
             "data": "synthetic (Ising initial tensor and its beta-derivative from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, steps {GROWTH_STEPS + args.warmup + 1}-"
                                    f"{GROWTH_STEPS + args.warmup + K} timed",
-                       "precision": "fp64", "z2_blocks": False,
+                       "precision": args.precision, "z2_blocks": False,
                        "l2": "inputs larger than L2 (per-slice operands and their derivatives)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ln_z_per_site": lnz,
@@ -499,16 +523,123 @@ def energy_arm(args):
             "rel_err_energy_vs_richardson_extrapolated_difference":
                 abs(dlnz - (fds[1e-5] - (fds[1e-4] - fds[1e-5]) / 99.0)) / abs(fd),
             "degenerate_pairs": degenerate,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                         "frac": achieved / 1.25 if achieved else None, "traffic": None,
-                         "peak_source": "nominal GB300 FP64 (no measured FP64 peak)",
-                         "note": "bottleneck region per c'-slice: three FP64 GEMMs of 2 R^2 Nc flops "
-                                 "(C, T^.dB^T, dT^.B^T) and one vector add"},
+            "roofline": roof,
             "e2e": None,
             "e2e_note": "inputs are beta and h only (the tensors are built on the device); "
                         "the end-to-end contract of the default workload does not apply",
             "gpu_launches": launches,
             "clocks": clocks,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def energy_scan_arm(args):
+    """Differentiation form over a beta scan: 32 instances (beta uniform in [0.21, 0.23])
+    carrying d/d beta, stepped together by hotrg_step_batch; the internal energy u(beta)
+    after the last step and the specific heat c = -beta^2 du/dbeta by central differences
+    on the grid; the middle instance's energy checked against central differences of FP64
+    runs.  Metric: instance-steps/s."""
+    import torch
+
+    import paper_2110_03607_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    betas = [0.21 + 0.02 * i / 31.0 for i in range(32)]
+    n = len(betas)
+    streams = [torch.cuda.Stream() for _ in range(n)]
+    ctxs = []
+    for b, st in zip(betas, streams):
+        c = pkg.hotrg_init_ising(D, b, H)
+        pkg.hotrg_set_precision(c, prec)
+        pkg.hotrg_set_stream(c, st.cuda_stream)
+        pkg.hotrg_set_tangent(c, True)
+        ctxs.append(c)
+    total = GROWTH_STEPS + args.warmup + args.steps
+    axes = axes_for(total)
+    chis = [CHI] * n
+    for a in axes[: GROWTH_STEPS + args.warmup]:
+        pkg.hotrg_step_batch(ctxs, [a] * n, chis, args.batch_threads)
+    torch.cuda.synchronize()
+    timed = axes[GROWTH_STEPS + args.warmup:]
+    launches0 = pkg.hotrg_launch_count(ctxs[0])
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a in timed:
+        pkg.hotrg_step_batch(ctxs, [a] * n, chis, args.batch_threads)
+    torch.cuda.synchronize()
+    elapsed_ms = (time.perf_counter() - t0) * 1000.0
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    launches = pkg.hotrg_launch_count(ctxs[0]) - launches0
+    res = [pkg.hotrg_energy(c) for c in ctxs]
+    for c in ctxs:
+        pkg.hotrg_free(c)
+    u = [r[1] for r in res]
+    deg = sum(r[2] for r in res)
+    db_grid = betas[1] - betas[0]
+    heat = {f"{betas[i]:.5f}": -betas[i] ** 2 * (u[i + 1] - u[i - 1]) / (2 * db_grid) for i in range(1, n - 1)}
+    # the middle instance against central differences of FP64 runs (untimed)
+    mid = n // 2
+
+    def ln_z_at(b):
+        f = pkg.Hotrg(D, b, H, precision=pkg.PREC_FP64)
+        for a in axes:
+            f.step(a, CHI)
+        v = f.free_energy()[0]
+        f.close()
+        return v
+
+    fds = {db: (ln_z_at(betas[mid] + db) - ln_z_at(betas[mid] - db)) / (2 * db) for db in (1e-5, 1e-4)}
+    rich = fds[1e-5] - (fds[1e-4] - fds[1e-5]) / 99.0
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
+    K = len(timed)
+    value = whole_job_rate(n * K, world, elapsed_ms)
+    if rank == 0:
+        line = {
+            "metric": "3D-Ising chi=12 HOTRG instance-steps/s carrying d/d beta, 32-beta scan",
+            "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
+                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ", "fp64": "f64"}[args.precision],
+            "data": "synthetic (Ising initial tensors and their beta-derivatives from beta, h; no dataset)",
+            "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
+                                   f"{args.warmup} warm-up steps, {K} timed batch steps",
+                       "precision": args.precision, "instances": n,
+                       "host_workers": args.batch_threads,
+                       "l2": "not flushed: the 32 instances' operands (tens of GB) exceed L2 together",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "beta": betas,
+            "energy_per_site": u,
+            "specific_heat_per_site": heat,
+            "degenerate_pairs": deg,
+            "check_beta": betas[mid],
+            "rel_err_energy_vs_central_difference": abs(-u[mid] - fds[1e-5]) / abs(fds[1e-5]),
+            "rel_err_energy_vs_richardson_extrapolated_difference": abs(-u[mid] - rich) / abs(rich),
+            "roofline": None,
+            "roofline_note": "see the single-instance energy3d_chi12 line; kernels of different "
+                             "instances overlap here",
+            "e2e": None,
+            "gpu_launches": launches,
+            "clocks": sampler.summary(),
             "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
@@ -541,6 +672,8 @@ def main():
         return batch_arm(args)
     if args.workload == "energy3d_chi12":
         return energy_arm(args)
+    if args.workload == "energy3d_chi12_scan":
+        return energy_scan_arm(args)
 
     import torch
 

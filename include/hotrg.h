@@ -202,12 +202,16 @@ int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, 
  * of the new tensor by the product rule over its two copies of T and its
  * 2(d-1) isometries (Sec. 4.2.9); and of the trace bookkeeping (Secs. 4.1.1,
  * 4.2.16).  Pairs with |lambda_k - lambda_l| <= 1e-12 lambda_1 across the
- * cut have no derivative: their terms are left out, and counted when their
- * coupling |v_l . dA u_k| exceeds 1e-9 lambda_1.  While on, the contraction
- * runs densely in FP64 (not in split BF16, not in Z2 blocks; the Grams and
- * the eigen-solver keep the block form of hotrg_set_z2, whose eigenvectors
- * have exact parities) and a step costs about three times a forward FP64
- * step; hotrg_step waits once per step for the isometry choice.
+ * cut (1e-8 lambda_1 when the step's contraction is split BF16, whose rounding
+ * splits exact degeneracies by about that much) have no derivative: their
+ * terms are left out, and counted when their coupling |v_l . dA u_k| exceeds
+ * 1e-9 lambda_1.  While on, the contraction
+ * runs densely (not in Z2 blocks; the Grams and the eigen-solver keep the
+ * block form of hotrg_set_z2, whose eigenvectors have exact parities) in the
+ * arithmetic of hotrg_set_precision: FP64, or split BF16 on the tensor cores
+ * with the derivative's FP32 chain operands and an FP64 sum of dB before it
+ * is split.  A step costs about three dense forward steps; hotrg_step waits
+ * once per step for the isometry choice.
  * enable = 1 needs a context from hotrg_init_ising with beta > 0 and no step
  * yet (dT^(0) is the beta-derivative of Eq. 2.4); enable = 0 stops carrying
  * it.  hotrg_set_tensor turns it off.  Errors: EINVAL (not an Ising context,

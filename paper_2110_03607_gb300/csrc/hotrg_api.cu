@@ -187,6 +187,7 @@ struct hotrg_ctx {
   double h = 0.0;
   Buf dT, dT2, dTb, dXp, dS, dA, dU64, eG, eZ, eZt, rank, Yd, tstate;
   Buf dchA, dchB, dchT, dBp, tBp, dCb, tCb;
+  Buf dAp, dB64, dU32;   // split-BF16 form: pieces of dT, FP64 staging of dB, dU in FP32
 };
 
 namespace {
@@ -606,7 +607,7 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
               &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
               &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
               &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
-              &c->tCb};
+              &c->tCb, &c->dAp, &c->dB64, &c->dU32};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
@@ -655,9 +656,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   const long long RR = R * R;
   // bottleneck work of this step: 2 * R^2 * (P_new P) per c'-slice, chi_c slices
   const double bn_flops = 2.0 * (double)R * (double)R * (double)Pn * (double)P * (double)chi_c;
-  // the derivative d/d beta, when carried, runs with the FP64 dense form
+  // the derivative d/d beta, when carried, runs with the dense contraction
   const bool tangent = c->tangent != 0;
-  const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below || tangent;
+  const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below;
   c->last_fp64 = fp64 ? 1 : 0;
 
   if (c->profile != 2) {   // profile 2 keeps the marks of several steps
@@ -1202,9 +1203,14 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       launch_gemm_nn_f64(dAs, n, (const double*)c->U64.p + u_off[j], nn, G, nn, n, nn, n, 1, 0, 0, 0, s);
       launch_gemm_nn_f64(Vs, n, G, nn, (double*)c->eZ.p, nn, n, nn, n, 1, 0, 0, 0, s);    // v_i . dA u_k
       launch_eig_dscale((const double*)c->eZ.p, (const double*)c->lam.p + lam_off[j] + (long long)side * n,
-                        (const int*)c->rank.p + rank_off[j], n, nn, (double*)c->eZt.p, tst, s);
+                        (const int*)c->rank.p + rank_off[j], n, nn, fp64 ? 1e-12 : 1e-8, (double*)c->eZt.p,
+                        tst, s);
       launch_gemm_nn_f64((const double*)c->eZt.p, n, Vs, n, G, n, nn, n, n, 1, 0, 0, 0, s);   // dU^T
       launch_transpose(G, nn, n, (double*)c->dU64.p + u_off[j], s);
+    }
+    if (!fp64) {
+      CHECK_ALLOC(dev_alloc(c, c->dU32, sizeof(float) * u_total));
+      launch_narrow_f64((const double*)c->dU64.p, (float*)c->dU32.p, u_total, s);
     }
     if (pending_error(c, "the derivative of the isometries") != HOTRG_OK) return HOTRG_ECUDA;
   }
@@ -1235,9 +1241,10 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   int n1_chunk = nnew1;
   {
     // the Z2 blocks of B and C hold about half of B and C again; the derivative
-    // adds two more of B and C and three more chain buffers
+    // adds two more of B and C (and FP64 staging of dB in the split form) and three
+    // more chain buffers
     const double per_unit =
-        (z2 ? 1.6 : 1.0) * (tangent ? 3.0 : 1.0) * (double)(Ns / nnew1) *
+        (z2 ? 1.6 : 1.0) * (tangent ? (fp64 ? 3.0 : 4.0) : 1.0) * (double)(Ns / nnew1) *
             ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
         (tangent ? 5.0 : 2.0) * (double)elt * (double)chain_max / nnew1;
     size_t free_b = 0, total_b = 0;
@@ -1369,6 +1376,14 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
     if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
     if (!zfold) CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
+    if (tangent) {
+      CHECK_ALLOC(dev_alloc(c, c->dBp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->dBp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
+      CHECK_ALLOC(dev_alloc(c, c->dB64, sizeof(double) * Nsub * R));
+      CHECK_ALLOC(dev_alloc(c, c->tBp, sizeof(double) * Nsub * R));
+      CHECK_ALLOC(dev_alloc(c, c->dCb, sizeof(float) * R * Nsub));
+      CHECK_ALLOC(dev_alloc(c, c->tCb, sizeof(float) * R * Nsub));
+    }
     Phase ph(c, 4);
     if (z2) {
       CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(__nv_bfloat16) * npieces * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
@@ -1383,6 +1398,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
       if (Kpad != R) cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
       launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
+      if (tangent) {
+        CHECK_ALLOC(dev_alloc(c, c->dAp, sizeof(__nv_bfloat16) * npieces * R * Kpad));
+        if (Kpad != R) cudaMemsetAsync(c->dAp.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
+        launch_split_bf16((const double*)c->dT.p, R, R, R, (__nv_bfloat16*)c->dAp.p, Kpad, R * Kpad, npieces, s);
+      }
     }
   }
   double bn_done = 0.0;
@@ -1444,7 +1464,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     for (int k = 1; k < d; ++k) in.push_back({I_NC + k, chij[k], rs[k]});
     for (int k = 1; k < d; ++k) in.push_back({I_NCP + k, chij[k], cs[k]});
     const void* src = Tc + (long long)sl * cs[0];
-    const double* dsrc = tangent ? (const double*)c->dT.p + (long long)sl * cs[0] : nullptr;
+    const void* dsrc = tangent ? (const double*)c->dT.p + (long long)sl * cs[0] : nullptr;
     int src_f64 = 1;
     for (int j = 1; j < d; ++j) {
       Phase ph(c, 5);
@@ -1479,12 +1499,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         if (tangent) {   // dX_j = stage(dX_{j-1}, U) + stage(X_{j-1}, dU)
           double* ddst = last ? (double*)c->dBp.p : (double*)((j & 1) ? c->dchA.p : c->dchB.p);
           double* tdst = last ? (double*)c->tBp.p : (double*)c->dchT.p;
-          launch_chain_f64(cd, dsrc, (const double*)c->U64.p + u_off[j] + ucol, ddst, s);
+          launch_chain_f64(cd, (const double*)dsrc, (const double*)c->U64.p + u_off[j] + ucol, ddst, s);
           launch_chain_f64(cd, (const double*)src, (const double*)c->dU64.p + u_off[j] + ucol, tdst, s);
           launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
           dsrc = ddst;
         }
-      } else if (c->f64_chains) {
+      } else if (c->f64_chains && !tangent) {
         cd.npieces = npieces;
         cd.piece_stride = Nc * Kpad;
         launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j] + ucol, dst,
@@ -1494,9 +1514,37 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         cd.piece_stride = Nc * Kpad;
         launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, dst,
                          last ? OUT_BF16_SPLIT : OUT_F32, s);
+        if (tangent) {   // the same in FP32; the last stage sums in FP64 (row pitch R), then splits
+          ChainDesc cdt = cd;
+          if (last) {
+            View outT;
+            for (int k = 1; k < d; ++k) outT.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P * R});
+            for (int k = 1; k < d; ++k) outT.push_back({I_NC + k, chij[k], prod_after(chij, k) * R});
+            outT.push_back({I_RHO, chi_c, P});
+            for (int k = 1; k < d; ++k) outT.push_back({I_NHP + k, chij[k], prod_after(chij, k)});
+            if (!make_stage(cdt, in, outT, I_NHP + j, I_NCP + j, I_NP + j, chij[j], nsz[j])) {
+              c->poisoned = HOTRG_EINVAL;
+              return HOTRG_EINVAL;
+            }
+            cdt.ldu = nnew[j];
+          }
+          void* ddst = last ? c->dB64.p : ((j & 1) ? c->dchA.p : c->dchB.p);
+          void* tdst = last ? c->tBp.p : c->dchT.p;
+          const int mode = last ? OUT_F64 : OUT_F32;
+          launch_chain_f32(cdt, dsrc, src_f64, (const float*)c->U32.p + u_off[j] + ucol, ddst, mode, s);
+          launch_chain_f32(cdt, src, src_f64, (const float*)c->dU32.p + u_off[j] + ucol, tdst, mode, s);
+          if (last) {
+            launch_axpby(1.0, (const double*)tdst, 1.0, (double*)ddst, Nc * R, s);
+            launch_split_bf16((const double*)ddst, Nc, R, R, (__nv_bfloat16*)c->dBp.p, Kpad, Nc * Kpad, npieces,
+                              s);
+          } else {
+            launch_add_f32((const float*)tdst, (float*)ddst, view_elems(out), s);
+          }
+          dsrc = ddst;
+        }
       }
       src = dst;
-      src_f64 = (fp64 || c->f64_chains) ? 1 : 0;
+      src_f64 = (fp64 || (c->f64_chains && !tangent)) ? 1 : 0;
       in = out;
     }
     if (pending_error(c, "the prime chain") != HOTRG_OK) return HOTRG_ECUDA;
@@ -1574,6 +1622,16 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                          (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Nc,
                          &((DevState*)c->state.p)->status, s, nullptr) != 0)
         return launch_failed(c, "tensor-core GEMM", R, Nc, Kpad);
+      if (tangent) {   // dC = T^ . dB^T + dT^ . B^T
+        if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->dBp.p, (int)Nc,
+                           (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->dCb.p, Nc,
+                           &((DevState*)c->state.p)->status, s, nullptr) != 0 ||
+            launch_tc_gemm((const __nv_bfloat16*)c->dAp.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
+                           (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->tCb.p, Nc,
+                           &((DevState*)c->state.p)->status, s, nullptr) != 0)
+          return launch_failed(c, "tensor-core GEMM (derivative)", R, Nc, Kpad);
+        launch_add_f32((const float*)c->tCb.p, (float*)c->dCb.p, R * Nc, s);
+      }
     }
     }
     if (pending_error(c, "the bottleneck") != HOTRG_OK) return HOTRG_ECUDA;
@@ -1586,7 +1644,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     for (int k = 1; k < d; ++k) cin.push_back({I_NP + k, nsz[k], prod_after(nnew, k) * P});
     for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
     const void* csrc = c->Cb.p;
-    const double* dcsrc = tangent ? (const double*)c->dCb.p : nullptr;
+    const void* dcsrc = tangent ? c->dCb.p : nullptr;
     for (int j = d - 1; j >= 1; --j) {
       Phase ph(c, 7);
       View out;
@@ -1617,12 +1675,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           const long long slab = (long long)sl * Pn + (long long)n1lo * prod_after(nnew, 1);
           double* ddst = last ? dTn + slab : (double*)((j & 1) ? c->dchA.p : c->dchB.p);
           double* tdst = last ? dTn2 + slab : (double*)c->dchT.p;
-          launch_chain_f64(cd, dcsrc, (const double*)c->U64.p + u_off[j], ddst, s);
+          launch_chain_f64(cd, (const double*)dcsrc, (const double*)c->U64.p + u_off[j], ddst, s);
           launch_chain_f64(cd, (const double*)csrc, (const double*)c->dU64.p + u_off[j], tdst, s);
           if (!last) launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
           dcsrc = ddst;
         }
-      } else if (c->f64_chains) {
+      } else if (c->f64_chains && !tangent) {
         launch_chain_f64acc(cd, csrc, j == d - 1 ? 0 : 1, (const double*)c->U64.p + u_off[j], dst, OUT_F64, s);
       } else if (zfold && j == d - 1) {
         const Z2Chunk& ch = zch[n1lo / n1_chunk];
@@ -1638,6 +1696,16 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
       } else {
         launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
+        if (tangent) {   // the same in FP32 (FP64 output of the last stage)
+          const long long slab = (long long)sl * Pn + (long long)n1lo * prod_after(nnew, 1);
+          void* ddst = last ? (void*)(dTn + slab) : ((j & 1) ? c->dchA.p : c->dchB.p);
+          void* tdst = last ? (void*)(dTn2 + slab) : c->dchT.p;
+          const int mode = last ? OUT_F64 : OUT_F32;
+          launch_chain_f32(cd, dcsrc, 0, (const float*)c->U32.p + u_off[j], ddst, mode, s);
+          launch_chain_f32(cd, csrc, 0, (const float*)c->dU32.p + u_off[j], tdst, mode, s);
+          if (!last) launch_add_f32((const float*)tdst, (float*)ddst, view_elems(out), s);
+          dcsrc = ddst;
+        }
       }
       csrc = dst;
       cin = out;
@@ -2065,7 +2133,7 @@ void hotrg_free(hotrg_ctx* c) {
               &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
               &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
               &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
-              &c->tCb};
+              &c->tCb, &c->dAp, &c->dB64, &c->dU32};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);

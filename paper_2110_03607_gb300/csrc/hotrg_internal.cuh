@@ -178,10 +178,12 @@ void launch_init_ising_dbeta(double* dT, int d, double beta, double h, cudaStrea
 void launch_sym_sum(const double* parts, int nsplit, int m, double* dS, cudaStream_t s);
 void launch_assemble_dot(const double* sh, const double* dsh, const double* sc, const double* dsc, int chi_j,
                          int chi_c, double* dA, cudaStream_t s);
-void launch_eig_dscale(const double* Z, const double* lam_sorted, const int* rank, int n, int nnew, double* Zt,
-                       TanState* tst, cudaStream_t s);
+void launch_eig_dscale(const double* Z, const double* lam_sorted, const int* rank, int n, int nnew,
+                       double rel_tol, double* Zt, TanState* tst, cudaStream_t s);
 void launch_transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
 void launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+void launch_add_f32(const float* x, float* y, long long n, cudaStream_t s);
+void launch_narrow_f64(const double* in, float* out, long long n, cudaStream_t s);
 void launch_finish_tangent(const double* Yd, int chi_c, const DevState* st, TanState* tst, int p, int first,
                            cudaStream_t s);
 void launch_tangent_scale(const double* dT, const double* That, double* out, long long n, const DevState* st,

@@ -101,13 +101,15 @@ void launch_assemble_dot(const double* sh, const double* dsh, const double* sc, 
 // du_k = sum over discarded l of v_l (v_l . dA u_k) / (lam_k - lam_l).  Input
 // Z[i][k] = v_i . dA u_k over the unsorted eigenvectors i, whose rank in the sorted
 // order is rank[i]; output Zt[k][i] = Z[i][k] / (lam_k - lam_i) for discarded i, else 0.
-// Pairs closer than 1e-12 lam_1 have no derivative: left out, and counted unless their
+// Pairs closer than rel_tol lam_1 have no derivative: left out, and counted unless their
 // coupling |Z| is below 1e-9 lam_1 (a pair kept apart by a symmetry of dA, e.g. of
-// opposite Z2 parity, couples with Z = 0).
+// opposite Z2 parity, couples with Z = 0).  rel_tol is 1e-12 with an FP64 contraction
+// and 1e-8 with the split-BF16 one, whose rounding (not symmetric under the lattice
+// symmetries) splits exactly degenerate pairs by about that much.
 __global__ void eig_dscale_kernel(const double* __restrict__ Z, const double* __restrict__ lam_sorted,
-                                  const int* __restrict__ rank, int n, int nnew, double* __restrict__ Zt,
-                                  TanState* tst) {
-  const double tol = 1e-12 * lam_sorted[0];
+                                  const int* __restrict__ rank, int n, int nnew, double rel_tol,
+                                  double* __restrict__ Zt, TanState* tst) {
+  const double tol = rel_tol * lam_sorted[0];
   const int total = n * nnew;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int k = e / n, i = e % n;
@@ -123,9 +125,9 @@ __global__ void eig_dscale_kernel(const double* __restrict__ Z, const double* __
   }
 }
 
-void launch_eig_dscale(const double* Z, const double* lam_sorted, const int* rank, int n, int nnew, double* Zt,
-                       TanState* tst, cudaStream_t s) {
-  eig_dscale_kernel<<<tgrid((long long)n * nnew), 256, 0, s>>>(Z, lam_sorted, rank, n, nnew, Zt, tst);
+void launch_eig_dscale(const double* Z, const double* lam_sorted, const int* rank, int n, int nnew,
+                       double rel_tol, double* Zt, TanState* tst, cudaStream_t s) {
+  eig_dscale_kernel<<<tgrid((long long)n * nnew), 256, 0, s>>>(Z, lam_sorted, rank, n, nnew, rel_tol, Zt, tst);
   ++g_launches;
 }
 
@@ -153,6 +155,28 @@ __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, d
 
 void launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
   axpby_kernel<<<tgrid(n), 256, 0, s>>>(a, x, b, y, n);
+  ++g_launches;
+}
+
+// y[i] += x[i] (FP32 chain operands of the split-BF16 form)
+__global__ void add_f32_kernel(const float* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+void launch_add_f32(const float* x, float* y, long long n, cudaStream_t s) {
+  add_f32_kernel<<<tgrid(n), 256, 0, s>>>(x, y, n);
+  ++g_launches;
+}
+
+// out[i] = (float)in[i]
+__global__ void narrow_f64_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+void launch_narrow_f64(const double* in, float* out, long long n, cudaStream_t s) {
+  narrow_f64_kernel<<<tgrid(n), 256, 0, s>>>(in, out, n);
   ++g_launches;
 }
 
