@@ -622,6 +622,7 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
       return cuda_status(c);
   }
   CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
+  if (c->tangent) CHECK_ALLOC(dev_alloc(c, c->Yd, sizeof(double) * kMaxBond * kMaxBond));
   return HOTRG_OK;
 }
 

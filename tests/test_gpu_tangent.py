@@ -154,6 +154,60 @@ def test_energy_against_onsager(pkg, beta, chi, gate):
     assert abs(u - exact) / abs(exact) <= gate, (u, exact, deg)
 
 
+def test_batch_of_tangent_contexts_equals_separate_runs(pkg):
+    # the scan path: contexts carrying the derivative, stepped together on their own streams
+    import torch
+
+    insts = [(3, 0.215, 0.0, 6), (3, 0.22, 0.01, 8), (2, 0.4, 0.0, 10)]
+    axes = [0, 1, 2, 0, 1, 2]
+    alone = []
+    for d, b, h, chi in insts:
+        res, _ = _gpu_tangent_run(pkg, d, b, h, chi, [a % d for a in axes], prec=2, fp64_below=0.0)
+        alone.append(res[-1])
+    streams = [torch.cuda.Stream() for _ in insts]
+    ctxs = []
+    try:
+        for (d, b, h, chi), st in zip(insts, streams):
+            c = pkg.hotrg_init_ising(d, b, h)
+            pkg.hotrg_set_precision(c, 2)
+            pkg.hotrg_set_fp64_threshold(c, 0.0)
+            pkg.hotrg_set_stream(c, st.cuda_stream)
+            pkg.hotrg_set_tangent(c, True)
+            ctxs.append(c)
+        for a in axes:
+            pkg.hotrg_step_batch(ctxs, [a % d for d, _, _, _ in insts], [x[3] for x in insts], 3)
+        for c, ref in zip(ctxs, alone):
+            dlnz, u, deg = pkg.hotrg_energy(c)
+            assert (dlnz, deg) == (ref[0], ref[2])
+    finally:
+        for c in ctxs:
+            pkg.hotrg_free(c)
+
+
+def test_allocator_switch_keeps_the_derivative(pkg):
+    # hotrg_set_allocator drops the workspaces but keeps T, dT and both run states
+    import torch
+
+    axes = o.cyclic_axes(3, 5)
+    ref, _ = _gpu_tangent_run(pkg, 3, 0.22, 0.0, 6, axes)
+    c = pkg.hotrg_init_ising(3, 0.22, 0.0)
+    g = None
+    try:
+        pkg.hotrg_set_precision(c, 0)
+        pkg.hotrg_set_stream(c, torch.cuda.current_stream().cuda_stream)
+        pkg.hotrg_set_tangent(c, True)
+        for a in axes[:2]:
+            pkg.hotrg_step(c, a, 6)
+        g = pkg.Hotrg.__new__(pkg.Hotrg)   # borrow the torch hooks of the owning handle
+        g.ctx = c
+        g.use_torch()
+        for a in axes[2:]:
+            pkg.hotrg_step(c, a, 6)
+        assert pkg.hotrg_energy(c)[0] == ref[-1][0]
+    finally:
+        pkg.hotrg_free(c)
+
+
 def test_bad_arguments(pkg):
     g = pkg.Hotrg(2, 0.3, 0.0)
     try:
