@@ -191,21 +191,20 @@ def test_allocator_switch_keeps_the_derivative(pkg):
     axes = o.cyclic_axes(3, 5)
     ref, _ = _gpu_tangent_run(pkg, 3, 0.22, 0.0, 6, axes)
     c = pkg.hotrg_init_ising(3, 0.22, 0.0)
-    g = None
+    g = pkg.Hotrg.__new__(pkg.Hotrg)   # owning handle around the raw context (frees it once)
+    g.ctx, g._cb = c, None
     try:
         pkg.hotrg_set_precision(c, 0)
         pkg.hotrg_set_stream(c, torch.cuda.current_stream().cuda_stream)
         pkg.hotrg_set_tangent(c, True)
         for a in axes[:2]:
             pkg.hotrg_step(c, a, 6)
-        g = pkg.Hotrg.__new__(pkg.Hotrg)   # borrow the torch hooks of the owning handle
-        g.ctx = c
-        g.use_torch()
+        g.use_torch()                      # switch to the torch allocator mid-run
         for a in axes[2:]:
             pkg.hotrg_step(c, a, 6)
         assert pkg.hotrg_energy(c)[0] == ref[-1][0]
     finally:
-        pkg.hotrg_free(c)
+        g.close()
 
 
 def test_bad_arguments(pkg):
