@@ -1183,6 +1183,35 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         long long size[kMaxDims], ist[kMaxDims];
         int pslot[kMaxDims];
         const int nd = gram_dims(j, kind, size, ist, pslot);
+        if (z2g) {   // parity blocks, as for the step's own Grams: P_b = dX_b X_b^T
+          const long long* zg = (const long long*)c->Zg.p;
+          double* X = (double*)c->Xp.p;
+          double* dX = (double*)c->dXp.p;
+          launch_z2_gather_rc(Tc, zg + gz_roff[j][kind], (int)m, zg + gz_koff[j][kind], K, X, s);
+          launch_z2_gather_rc((const double*)c->dT.p, zg + gz_roff[j][kind], (int)m, zg + gz_koff[j][kind], K, dX,
+                              s);
+          const double* pb[2] = {(const double*)c->parts.p, (const double*)c->parts.p};
+          int nsb[2] = {0, 0};
+          long long poff = 0;
+          for (int b = 0; b < 2; ++b) {
+            const long long mb = gz_mb[j][b], Kb = gz_Kb[j][kind][b];
+            if (mb == 0 || Kb == 0) continue;
+            const long long r0 = b == 0 ? 0 : gz_mb[j][0], q0 = b == 0 ? 0 : gz_Kb[j][kind][0];
+            const int nsplit = gram_splits(mb, Kb);
+            double* pdst = (double*)c->parts.p + poff;
+            launch_gemm_nt_f64(dX + r0 * K + q0, K, X + r0 * K + q0, K, pdst, mb, mb * mb, (int)mb, (int)mb, Kb,
+                               nsplit, 0, s);
+            long long kchunk = (Kb + nsplit - 1) / nsplit;
+            kchunk = (kchunk + 15) / 16 * 16;
+            nsb[b] = (int)((Kb + kchunk - 1) / kchunk);
+            pb[b] = pdst;
+            poff += (long long)nsb[b] * mb * mb;
+          }
+          const int* zi = (const int*)(zg + gz_n64) + gz_rowmap[j];
+          launch_z2_reduce_sum_t(pb[0], nsb[0], (int)gz_mb[j][0], pb[1], nsb[1], (int)gz_mb[j][1], zi, zi + m,
+                                 (int)m, dS0 + kind * mmax * mmax, s);
+          continue;
+        }
         launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
         launch_permute((const double*)c->dT.p, (double*)c->dXp.p, nd, size, ist, 1.0, s);
         const int nsplit = gram_splits(m, K);
@@ -1534,10 +1563,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           const int mode = last ? OUT_F64 : OUT_F32;
           launch_chain_f32(cdt, dsrc, src_f64, (const float*)c->U32.p + u_off[j] + ucol, ddst, mode, s);
           launch_chain_f32(cdt, src, src_f64, (const float*)c->dU32.p + u_off[j] + ucol, tdst, mode, s);
-          if (last) {
-            launch_axpby(1.0, (const double*)tdst, 1.0, (double*)ddst, Nc * R, s);
+          if (last) {   // dB = both terms, summed in FP64 as they are split
             launch_split_bf16((const double*)ddst, Nc, R, R, (__nv_bfloat16*)c->dBp.p, Kpad, Nc * Kpad, npieces,
-                              s);
+                              s, (const double*)tdst);
           } else {
             launch_add_f32((const float*)tdst, (float*)ddst, view_elems(out), s);
           }

@@ -73,7 +73,7 @@ void launch_permute(const double* in, double* out, int ndim, const long long* ou
                     const long long* in_stride, double scale, cudaStream_t s);
 void launch_split_bf16(const double* in, long long rows, long long cols, long long ld_in,
                        __nv_bfloat16* out, long long ld_out, long long piece_stride, int npieces,
-                       cudaStream_t s);
+                       cudaStream_t s, const double* in2 = nullptr);
 void launch_trace_y(const double* Tn, int chi_c, long long pn, double* Y, cudaStream_t s);
 void launch_finish_step(double* Y, int chi_c, DevState* st, int p, int first, cudaStream_t s);
 void launch_scale(const double* in, double* out, long long n, const DevState* st, cudaStream_t s);
@@ -146,6 +146,8 @@ void launch_z2_gather_rc(const double* T, const long long* roff, int m, const lo
                          long long K, double* X, cudaStream_t s);
 void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
                           const int* blk, const int* pos, int m, double* S, cudaStream_t s);
+void launch_z2_reduce_sum_t(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
+                            const int* blk, const int* pos, int m, double* dS, cudaStream_t s);
 void launch_z2_gather_split(const double* src, long long ld, const int* rowmap, int nrows,
                             const int* colmap, int ncols, __nv_bfloat16* dst, long long piece_stride,
                             int npieces, cudaStream_t s);

@@ -84,15 +84,16 @@ void launch_permute(const double* in, double* out, int ndim, const long long* ou
   ++g_launches;
 }
 
-// FP64 -> npieces BF16 pieces: p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1).
-__global__ void split_bf16_kernel(const double* __restrict__ in, long long rows, long long cols,
-                                  long long ld_in, __nv_bfloat16* __restrict__ out, long long ld_out,
-                                  long long piece_stride, int npieces) {
+// FP64 -> npieces BF16 pieces: p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1),
+// with x = in (+ in2, the same layout, when given).
+__global__ void split_bf16_kernel(const double* __restrict__ in, const double* __restrict__ in2, long long rows,
+                                  long long cols, long long ld_in, __nv_bfloat16* __restrict__ out,
+                                  long long ld_out, long long piece_stride, int npieces) {
   long long total = rows * cols;
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
     long long r = e / cols, c = e - r * cols;
-    double x = in[r * ld_in + c];
+    double x = in2 ? in[r * ld_in + c] + in2[r * ld_in + c] : in[r * ld_in + c];
     long long o = r * ld_out + c;
     for (int p = 0; p < npieces; ++p) {
       __nv_bfloat16 b = __double2bfloat16(x);
@@ -104,12 +105,12 @@ __global__ void split_bf16_kernel(const double* __restrict__ in, long long rows,
 
 void launch_split_bf16(const double* in, long long rows, long long cols, long long ld_in,
                        __nv_bfloat16* out, long long ld_out, long long piece_stride, int npieces,
-                       cudaStream_t s) {
+                       cudaStream_t s, const double* in2) {
   long long total = rows * cols;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
-  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, rows, cols, ld_in, out, ld_out,
+  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, in2, rows, cols, ld_in, out, ld_out,
                                                      piece_stride, npieces);
   ++g_launches;
 }

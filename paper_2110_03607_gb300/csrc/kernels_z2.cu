@@ -241,6 +241,38 @@ void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, i
   ++g_launches;
 }
 
+// The derivative of a Gram from its parity blocks: dS[i][j] = sum_z (P_b[z][p_i][p_j] +
+// P_b[z][p_j][p_i]) if rows i and j are both of parity b, else 0; P_b holds ns_b split-K
+// partials of the full m_b x m_b block product dX_b X_b^T.
+__global__ void z2_reduce_sum_t_kernel(const double* __restrict__ p0, int ns0, int m0,
+                                       const double* __restrict__ p1, int ns1, int m1,
+                                       const int* __restrict__ blk, const int* __restrict__ pos, int m,
+                                       double* __restrict__ dS) {
+  const long long total = (long long)m * m;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e - (long long)i * m);
+    double acc = 0.0;
+    const int b = blk[i];
+    if (b == blk[j]) {
+      const int pi = pos[i], pj = pos[j];
+      const double* p = b == 0 ? p0 : p1;
+      const int mb = b == 0 ? m0 : m1, ns = b == 0 ? ns0 : ns1;
+      const long long bb = (long long)mb * mb;
+      for (int z = 0; z < ns; ++z)
+        acc += p[z * bb + (long long)pi * mb + pj] + p[z * bb + (long long)pj * mb + pi];
+    }
+    dS[e] = acc;
+  }
+}
+
+void launch_z2_reduce_sum_t(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
+                            const int* blk, const int* pos, int m, double* dS, cudaStream_t s) {
+  z2_reduce_sum_t_kernel<<<grid_for((long long)m * m), 256, 0, s>>>(p0, ns0, m0, p1, ns1, m1, blk, pos,
+                                                                    m, dS);
+  ++g_launches;
+}
+
 // Eigen-decomposition in parity blocks (Sec. 4.2.5): A^(j) is block diagonal in the
 // parity of its composite index (hat, check), so each block is decomposed on its own.
 // Ab[p][q] = A[rows[p]][rows[q]] for p, q < nb, zero-padded to npad x npad (a zero row and
