@@ -121,3 +121,21 @@ def onsager_energy_per_site(beta: float) -> float:
     k = 2.0 * math.sinh(2 * beta) / math.cosh(2 * beta) ** 2
     kk = special.ellipk(k * k)
     return -(1.0 / math.tanh(2 * beta)) * (1.0 + (2.0 / math.pi) * (2.0 * math.tanh(2 * beta) ** 2 - 1.0) * kk)
+
+
+def brute_force_specific_heat(shape: tuple, beta: float, h: float) -> float:
+    """c = beta^2 d^2(ln Z / N)/d beta^2 = beta^2 (<H^2> - <H>^2) / N by enumeration."""
+    n = int(np.prod(shape))
+    if n > 24:
+        raise ValueError("lattice too large for brute force")
+    states = np.array(list(itertools.product([1.0, -1.0], repeat=n))).reshape((-1,) + tuple(shape))
+    bonds = np.zeros(states.shape[0])
+    for k in range(len(shape)):
+        bonds += (states * np.roll(states, -1, axis=1 + k)).reshape(states.shape[0], -1).sum(1)
+    mag = states.reshape(states.shape[0], -1).sum(1)
+    energy = -(bonds + h * mag)
+    expo = -beta * energy
+    w = np.exp(expo - expo.max())
+    w /= w.sum()
+    mean = (w * energy).sum()
+    return float(beta * beta * ((w * (energy - mean) ** 2).sum()) / n)

@@ -185,3 +185,21 @@ def test_energy_chi8_20_steps_against_onsager(beta, gate):
     assert abs(rec.energy_per_site - exact) / abs(exact) <= gate
     # a sign error or the missing 1/V would be far outside the gate
     assert abs(-rec.energy_per_site - exact) / abs(exact) > 1.0
+
+
+@pytest.mark.parametrize("d,nsteps,chi,beta,h", [(2, 4, 16, 0.35, 0.0), (3, 3, 16, 0.25, 0.05)])
+def test_specific_heat_from_energies_equals_brute_force(d, nsteps, chi, beta, h):
+    # c = -beta^2 du/dbeta from central differences of the tangent run's energy (the way
+    # the beta scan reports it), on lattices the run builds without truncation
+    axes = o.cyclic_axes(d, nsteps, first=d - 1)
+    db = 1e-4
+
+    def energy(b):
+        r = tg.HotrgTangentRun(d, b, h)
+        for a in axes:
+            rec = r.step(a, chi)
+        return rec.energy_per_site
+
+    c = -beta ** 2 * (energy(beta + db) - energy(beta - db)) / (2 * db)
+    exact = ex.brute_force_specific_heat(ex.lattice_after(d, axes), beta, h)
+    assert c == pytest.approx(exact, rel=1e-6)
