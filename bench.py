@@ -1,7 +1,9 @@
 """Benchmark: HOTRG coarse-graining steps/s on one GB300 (per rank).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|fp64]
-                    [--workload ising3d_chi16|ising3d_chi20|ising4d_chi6] [--impl ours|reference]
+                    [--workload ising3d_chi16|ising3d_chi20|ising4d_chi6|ising4d_chi13|ising4d_chi14|
+                                batch3d_mixed|energy3d_chi12|energy3d_chi12_scan]
+                    [--z2 on|off] [--impl ours|reference]
 
 Default workload: 3D Ising, d = 3, chi = 16, beta = 0.2216544, h = 0, axes cycling
 z, x, y.  The first steps grow the bonds (2 -> 4 -> 16 for the default) and are not
@@ -11,6 +13,12 @@ chain, bottleneck, non-prime chain, trace/normalisation).  The local tensor (134
 FP64 for the default) and the per-slice operands (GBs) exceed the 129 MB L2.
 Per-step ln Z/V is compared with the FP64 oracle's reference values in
 tests/golden/<workload>.jsonl where those exist.
+
+Other workloads: the paper-shape 4D steps (ising4d_chi13/14), the batching form
+(batch3d_mixed: 64 independent instances stepped together) and the differentiation form
+(energy3d_chi12: steps carrying d/d beta, the internal energy checked against central
+differences of FP64 runs; energy3d_chi12_scan: 32 beta in [0.21, 0.23] with energy and
+specific heat).
 
 Multi-GPU: independent replicas (one run per rank), weak scaling, no
 collective on the data path; rank 0 prints one JSON line.
