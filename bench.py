@@ -234,6 +234,47 @@ def oracle_step_sample(run, axis, sample_iters):
                                                    contraction_iters_total=total_iters)
 
 
+def fp64_form_leg(pkg, args, nsteps=2):
+    """The plain FP64 form of the same workload on the GPU: the bond-growth steps, then
+    `nsteps` steady steps timed with CUDA events (the first steady steps, where the Z2
+    blocks are balanced: its cheapest steps), their ln Z/V against the oracle's reference,
+    and the FP64 bottleneck rate as a fraction of the measured FP64 FMA rate."""
+    import torch
+
+    peak = pkg.hotrg_fp64_rate()
+    stream = torch.cuda.current_stream()
+    f = pkg.Hotrg(D, BETA, H, precision=pkg.PREC_FP64, z2=args.z2 == "on")
+    axes = axes_for(GROWTH_STEPS + nsteps)
+    for a in axes[:GROWTH_STEPS]:
+        f.step(a, CHI)
+    f.free_energy()
+    pkg.hotrg_profile(f.ctx, 2)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    done = 0.0
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for a in axes[GROWTH_STEPS:]:
+        f.step(a, CHI)
+        done += pkg.hotrg_bottleneck_flops(f.ctx)[1]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / nsteps
+    gemm_ms, gemm_n, _ = pkg.hotrg_step_times(f.ctx)
+    lnz = f.free_energy()[0]
+    f.close()
+    golden = load_golden()
+    last = GROWTH_STEPS + nsteps
+    achieved = done / (gemm_ms["bottleneck"] / 1000.0) / 1e12 if gemm_ms["bottleneck"] > 0 else None
+    return {"precision": "fp64", "steps_timed": f"{GROWTH_STEPS + 1}-{last}", "ms_per_step": ms,
+            "steps_per_s": 1000.0 / ms,
+            "rel_err_lnz_per_site_vs_oracle": abs(lnz - golden[last]) / abs(golden[last]) if last in golden else None,
+            "bottleneck_flops_per_step": done / nsteps,
+            "bottleneck_tflops": achieved, "fp64_peak_tflops_measured": peak,
+            "frac_of_measured_fp64": achieved / peak if achieved else None,
+            "note": "first steady steps (balanced Z2 blocks); later steps keep more even states and cost more"}
+
+
 def cpu_baseline_leg():
     run = oracle_steady_tensor()
     est, info = oracle_step_sample(run, axes_for(GROWTH_STEPS + 1)[-1], 48)
@@ -665,6 +706,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the two timed steps of the plain FP64 form")
     ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host workers of the batching form (batch3d_mixed)")
@@ -782,9 +825,10 @@ def main():
     achieved = flops_per_launch / (bn_ms / 1000.0) / 1e12 if bn_ms > 0 else None
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25 if achieved else None, "traffic": None,
-                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+        fp64_peak = pkg.hotrg_fp64_rate()
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                "peak_source": "FP64 FMA rate measured in this run (hotrg_fp64_rate)"}
     else:
         # DRAM bytes (read + write) of one Z2 block GEMM launch from the ncu capture in
         # profiles/tc_gemm_kernel_ising3d_chi16_bf16x6.md (launch shape of the first steady
@@ -842,6 +886,12 @@ def main():
         g = ee
     g.close()
 
+    # ---- the plain FP64 form of the same workload, for the metric's comparison
+    fp64_form = None
+    if args.precision != "fp64" and not args.no_fp64_form and WORKLOAD == "ising3d_chi16":
+        fp64_form = fp64_form_leg(pkg, args)
+        fp64_form["split_form_speedup"] = (value / world) / fp64_form["steps_per_s"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD in ("ising3d_chi16", "ising4d_chi6"):
         cpu = cpu_baseline_leg()
@@ -873,6 +923,7 @@ def main():
             "rel_err_by_step": {str(k): v for k, v in sorted(errs.items())},
             "phases_ms_per_step": mean_phase,
             "roofline": roof,
+            "fp64_form": fp64_form,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,

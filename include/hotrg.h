@@ -190,6 +190,44 @@ int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
 int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
                      int* status);
 
+/* c'-slice shard of one step over W ranks (processes, one GPU each), each holding
+ * a context with the same local tensor (the paper's replication of T over its
+ * processes, Secs. 3.2 and 4.2.3-4.2.4).  A step along `axis` with `chi` is:
+ *   1. hotrg_shard_env(part = rank, nparts = W): this rank's share of every
+ *      environment Gram S^, S~, S^', S~' of Sec. 3.2 -- the sum over its part of
+ *      the summed index (the indices other than the free pair; of each Z2
+ *      parity block when the block form applies) -- written to S.  Layout:
+ *      transverse legs j = 1 .. d-1 of the step (lattice axis (axis + j) mod d),
+ *      for each the kinds S^ (free n_j, c'), S~ (n_j, c), S^' (n'_j, c'),
+ *      S~' (n'_j, c), each an m_j x m_j row-major FP64 matrix, m_j = chi_j chi_c,
+ *      concatenated; *n = 4 sum_j m_j^2 elements (set even when cap is too small).
+ *   2. the caller sums S over the ranks (an allreduce), then
+ *      hotrg_shard_isometries(S, n) on every rank: A^(j), A'^(j) (Sec. 4.2.4),
+ *      the eigen-solver (Sec. 4.2.5), the choice, truncation and gauge
+ *      (Secs. 4.2.6-4.2.8) and, at zero field, the new legs' parities.  Equal
+ *      summed Grams give every rank the same isometries.
+ *   3. hotrg_shard_contract(c_lo, c_hi): the new tensor's c'-slices [c_lo, c_hi)
+ *      (Sec. 4.2.9: prime chain, bottleneck, non-prime chain; no communication)
+ *      into `slices`: slice c' is the block T'[(c, n)][(c', n')] for every row
+ *      (c, n) and every n', Rn x Pn row-major (Rn = chi_c Pn, Pn = the product
+ *      of the new transverse bond dimensions), at (c' - c_lo) Rn Pn; *n =
+ *      (c_hi - c_lo) Rn Pn.
+ *   4. the caller gathers the slices of all ranks in c' order (an allgather),
+ *      then hotrg_shard_finish(slices, n = chi_c Rn Pn) on every rank: the new
+ *      tensor is installed and the trace, Y, X, ln Z bookkeeping and
+ *      normalisation of Secs. 4.1.1, 4.2.11-4.2.16 run as in hotrg_step.
+ * Every call is synchronous (S and slices may be host or device pointers).
+ * The result equals hotrg_step's up to the grouping of the Grams' sums.  Calls
+ * out of order return ESTATE; a step that carries d/d beta cannot be sharded
+ * (EINVAL).  Errors: EINVAL (bad part, range or size), ENOMEM, ECUDA, ESTATE,
+ * and the device failures of hotrg_step. */
+int hotrg_shard_env(hotrg_ctx* ctx, int axis, int chi, int part, int nparts, double* S, int64_t cap,
+                    int64_t* n);
+int hotrg_shard_isometries(hotrg_ctx* ctx, int axis, int chi, const double* S, int64_t n);
+int hotrg_shard_contract(hotrg_ctx* ctx, int axis, int chi, int c_lo, int c_hi, double* slices,
+                         int64_t cap, int64_t* n);
+int hotrg_shard_finish(hotrg_ctx* ctx, int axis, int chi, const double* slices, int64_t n);
+
 /* Differentiation form: carry dT = dT/d beta through every later step in
  * forward mode, so that hotrg_energy() returns d(ln Z/V)/d beta and the
  * internal energy u = -d(ln Z/V)/d beta of the HOTRG approximation (Sec. 2
@@ -284,9 +322,12 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
  * and C must be DEVICE pointers (FP64, row-major) owned by the caller, and all
  * scratch (BF16 pieces, FP32 product, error word) lives in one fixed
  * file-scope device array of HOTRG_NOALLOC_SCRATCH_BYTES (64 MiB) that every
- * GPU loading the library keeps until the process exits.  Sizes whose scratch
- * exceeds it -- 2*np*(M+N)*ceil64(K) + 4*M*N bytes, np = 2 (BF16X3) or 3 --
- * are rejected with HOTRG_EINVAL.  The first call on a device looks up the
+ * GPU loading the library keeps until the process exits.  In the BF16 modes
+ * the scratch is 256 + r(2*np*M*Kp) + r(2*np*N*Kp) + r(4*M*N) bytes, with
+ * np = 2 (BF16X3) or 3 (BF16X6), Kp = K rounded up to a multiple of 64 and
+ * r(x) = x rounded up to a multiple of 256; sizes whose scratch exceeds the
+ * array are rejected with HOTRG_EINVAL (the FP64 mode needs no scratch).  The
+ * size limits of hotrg_gemm_nt apply in every mode.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Work is enqueued on
  * `stream` (a cudaStream_t, NULL = legacy default stream) and the call
@@ -297,6 +338,25 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
 #define HOTRG_NOALLOC_SCRATCH_BYTES (64u << 20)
 int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double* A, const double* B,
                           double* C, void* stream);
+
+/* Rate probe of the bottleneck GEMM kernel alone: allocates operand pieces of
+ * an M x K and an N x K operand (BF16-exact values) and an FP32 product on the
+ * current device, launches the split-BF16 tensor-core GEMM of hotrg_gemm_nt
+ * once to warm up, then `iters` times back to back on the legacy default
+ * stream, and returns the mean milliseconds per launch (CUDA events).  For
+ * rooflines and tuning; the paper has no counterpart.  mode is
+ * HOTRG_PREC_BF16X3 or HOTRG_PREC_BF16X6.  Errors: EINVAL, ENOMEM, ECUDA,
+ * ETIMEOUT. */
+int hotrg_gemm_rate(int mode, int M, int N, int K, int iters, double* ms_per_launch);
+
+/* FP64 fused multiply-add rate of the current device, in TFLOP/s (2 flops per
+ * FMA): independent FMA chains on every SM, timed with CUDA events (best of
+ * two launches after one warm-up).  The denominator of the FP64 kernels'
+ * roofline (environment Grams, eigen-solver, the FP64 form of the
+ * contraction); the paper has no counterpart.  Synchronous on the legacy
+ * default stream; allocates 8 bytes per CTA for its outputs.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int hotrg_fp64_rate(double* tflops);
 
 /* Bytes of device memory the context holds now. */
 int hotrg_device_bytes(hotrg_ctx* ctx, size_t* bytes);

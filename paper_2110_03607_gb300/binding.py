@@ -79,6 +79,12 @@ def load():
         "hotrg_tangent_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
         "hotrg_profile": (I, [P, I]),
         "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "hotrg_fp64_rate": (I, [ctypes.POINTER(D)]),
+        "hotrg_gemm_rate": (I, [I, I, I, I, I, ctypes.POINTER(D)]),
+        "hotrg_shard_env": (I, [P, I, I, I, I, P, I64, ctypes.POINTER(I64)]),
+        "hotrg_shard_isometries": (I, [P, I, I, P, I64]),
+        "hotrg_shard_contract": (I, [P, I, I, I, I, P, I64, ctypes.POINTER(I64)]),
+        "hotrg_shard_finish": (I, [P, I, I, P, I64]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "hotrg_launch_count": (I, [P, ctypes.POINTER(I64)]),
         "hotrg_free": (None, [P]),
@@ -304,6 +310,67 @@ def hotrg_step_times(ctx):
     _check(load().hotrg_step_times(ctx, ms, nl, ctypes.byref(n), ctypes.byref(f64)), "hotrg_step_times")
     return ({PHASES[k]: ms[k] for k in range(n.value)}, {PHASES[k]: nl[k] for k in range(n.value)},
             bool(f64.value))
+
+
+def shard_sizes(ctx, axis: int, chi: int):
+    """(Gram elements, c'-slices, elements of one slice) of a sharded step along `axis`."""
+    dims = hotrg_bond_dims(ctx)
+    d = sum(1 for x in dims if x > 0)
+    chi_c = dims[axis]
+    grams, pn = 0, 1
+    for j in range(1, d):
+        cj = dims[(axis + j) % d]
+        grams += 4 * (cj * chi_c) ** 2
+        pn *= min(cj * cj, chi)
+    return grams, chi_c, chi_c * pn * pn
+
+
+def _buf_len(buf):
+    return int(buf.numel()) if hasattr(buf, "numel") and callable(buf.numel) else int(np.asarray(buf).size)
+
+
+def hotrg_shard_env(ctx, axis: int, chi: int, part: int, nparts: int, out=None):
+    """This rank's share of the step's environment Grams (numpy FP64, or `out`)."""
+    n = shard_sizes(ctx, axis, chi)[0]
+    if out is None:
+        out = np.zeros(n, dtype=np.float64)
+    got = ctypes.c_int64()
+    _check(load().hotrg_shard_env(ctx, axis, chi, part, nparts, _ptr(out), _buf_len(out), ctypes.byref(got)),
+           "hotrg_shard_env")
+    return out
+
+
+def hotrg_shard_isometries(ctx, axis: int, chi: int, grams):
+    _check(load().hotrg_shard_isometries(ctx, axis, chi, _ptr(grams), _buf_len(grams)), "hotrg_shard_isometries")
+
+
+def hotrg_shard_contract(ctx, axis: int, chi: int, c_lo: int, c_hi: int, out=None):
+    """The new tensor's c'-slices [c_lo, c_hi) (numpy FP64 [c_hi - c_lo][Rn][Pn], or `out`)."""
+    _, _, per = shard_sizes(ctx, axis, chi)
+    if out is None:
+        out = np.zeros((c_hi - c_lo) * per, dtype=np.float64)
+    got = ctypes.c_int64()
+    _check(load().hotrg_shard_contract(ctx, axis, chi, c_lo, c_hi, _ptr(out), _buf_len(out), ctypes.byref(got)),
+           "hotrg_shard_contract")
+    return out
+
+
+def hotrg_shard_finish(ctx, axis: int, chi: int, slices):
+    _check(load().hotrg_shard_finish(ctx, axis, chi, _ptr(slices), _buf_len(slices)), "hotrg_shard_finish")
+
+
+def hotrg_gemm_rate(mode: int, m: int, n: int, k: int, iters: int) -> float:
+    """Milliseconds per launch of the split-BF16 GEMM kernel on device-resident operands."""
+    v = ctypes.c_double()
+    _check(load().hotrg_gemm_rate(mode, m, n, k, iters, ctypes.byref(v)), "hotrg_gemm_rate")
+    return v.value
+
+
+def hotrg_fp64_rate() -> float:
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(load().hotrg_fp64_rate(ctypes.byref(v)), "hotrg_fp64_rate")
+    return v.value
 
 
 def hotrg_device_bytes(ctx) -> int:

@@ -188,6 +188,14 @@ struct hotrg_ctx {
   Buf dT, dT2, dTb, dXp, dS, dA, dU64, eG, eZ, eZt, rank, Yd, tstate;
   Buf dchA, dchB, dchT, dBp, tBp, dCb, tCb;
   Buf dAp, dB64, dU32;   // split-BF16 form: pieces of dT, FP64 staging of dB, dU in FP32
+  // c'-slice shard of a step (hotrg_shard_*): the isometries of (shard_axis, shard_chi)
+  // are installed and the new-leg parities derived from them are kept until the
+  // gathered new tensor is installed
+  int shard_ready = 0;
+  int shard_axis = -1, shard_chi = 0;
+  int shard_z2 = 0, shard_track = 0;
+  double shard_bn_done = 0.0;
+  std::vector<unsigned char> shard_par[kMaxD];
 };
 
 namespace {
@@ -297,15 +305,7 @@ void* pinned_stage(hotrg_ctx* c, size_t bytes) {
 // blocks), then 3 for the FP32 warm start
 constexpr int kCounters32 = 3 * 4 * kMaxD;
 
-int num_sms() {
-  static const int n = [] {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v < 1 ? 148 : v;
-  }();
-  return n;
-}
+int num_sms() { return sm_count(); }
 
 // A launch wrapper refused its arguments or the launch failed: report which, then the
 // CUDA error state (if any) decides the status
@@ -633,11 +633,40 @@ int hotrg_set_precision(hotrg_ctx* c, int mode) {
   return HOTRG_OK;
 }
 
-int hotrg_step(hotrg_ctx* c, int axis, int chi) {
+namespace {
+
+// One phase of a step split over ranks by c'-slices (hotrg_shard_*).  PH_FULL is
+// the whole step of one process.
+enum ShardPhase { PH_FULL = 0, PH_ENV = 1, PH_ISO = 2, PH_CONTRACT = 3, PH_FINISH = 4 };
+struct Shard {
+  int phase = PH_FULL;
+  int part = 0, nparts = 1;      // PH_ENV: this rank's share of each Gram's summed index
+  int c_lo = 0, c_hi = 0;        // PH_CONTRACT: the c'-slices [c_lo, c_hi)
+  double* out = nullptr;         // PH_ENV: partial Grams; PH_CONTRACT: slices
+  int64_t cap = 0;
+  int64_t* n_out = nullptr;
+  const double* in = nullptr;    // PH_ISO: summed Grams; PH_FINISH: every slice
+};
+
+int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh);
+
+}  // namespace
+
+int hotrg_step(hotrg_ctx* c, int axis, int chi) { return step_impl(c, axis, chi, Shard()); }
+
+namespace {
+
+int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   if (!c) return HOTRG_EINVAL;
   if (c->poisoned) return HOTRG_ESTATE;
   const int d = c->d;
   if (axis < 0 || axis >= d || chi < 1 || chi > 32) return HOTRG_EINVAL;
+  const int phase = sh.phase;
+  if (phase != PH_FULL && c->tangent) return HOTRG_EINVAL;   // the shard carries no derivative
+  if ((phase == PH_CONTRACT || phase == PH_FINISH) &&
+      (!c->shard_ready || c->shard_axis != axis || c->shard_chi != chi))
+    return HOTRG_ESTATE;
+  if (phase == PH_FULL || phase == PH_ENV) c->shard_ready = 0;
   cudaStream_t s = c->stream;
 
   // ---- slot order for this step: Current = axis, Next j = (axis + j) mod d
@@ -804,10 +833,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   // Z2 blocks of the Grams: the rows (free pair) and the summed index, both listed even
   // parity first, as element offsets into T; per leg the block and position of each row
   const bool z2g = c->z2_valid && c->z2_enabled;
+  const bool env_phase = phase == PH_FULL || phase == PH_ENV || phase == PH_ISO;
   long long gz_roff[kMaxD][4], gz_koff[kMaxD][4], gz_rowmap[kMaxD];
   long long gz_mb[kMaxD][2], gz_Kb[kMaxD][4][2], gz_n64 = 0, gz_eig[kMaxD];
   int eig_nb[kMaxD][2];
-  if (z2g) {
+  if (z2g && env_phase) {
     long long n64 = 0, n32 = 0;
     for (int j = 1; j < d; ++j) {
       const long long m = (long long)chij[j] * chi_c;
@@ -912,7 +942,17 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       c->hpin_pending = 1;
     }
   }
-  for (int j = 1; j < d; ++j) {
+  // the shard's layout of the Grams: legs j = 1 .. d-1, kinds 0 .. 3, each m_j x m_j
+  // row-major (m_j = chi_j chi_c), concatenated
+  long long shard_s_elems = 0;
+  for (int j = 1; j < d; ++j) shard_s_elems += 4LL * chij[j] * chi_c * chij[j] * chi_c;
+  if (phase == PH_ENV || phase == PH_ISO) {
+    if (sh.n_out) *sh.n_out = shard_s_elems;
+    if ((phase == PH_ENV && (!sh.out || sh.cap < shard_s_elems)) ||
+        (phase == PH_ISO && (!sh.in || sh.cap != shard_s_elems)))
+      return HOTRG_EINVAL;
+  }
+  for (int j = 1; j < d && env_phase; ++j) {
     Phase ph(c, 1);
     const long long m = (long long)chij[j] * chi_c;
     const long long K = RR / m;
@@ -921,6 +961,12 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       int pslot[kMaxDims];
       const int nd = gram_dims(j, kind, size, ist, pslot);
       double* Sdst = (double*)c->S.p + ((long long)(j - 1) * 4 + kind) * mmax * mmax;
+      if (phase == PH_ISO) continue;   // the summed Grams are installed below
+      // PH_ENV: this rank's part of the summed index (of each parity block)
+      auto kpart = [&](long long kk, long long* lo) {
+        *lo = kk * sh.part / sh.nparts;
+        return kk * (sh.part + 1) / sh.nparts - *lo;
+      };
       if (z2g) {
         const long long* zg = (const long long*)c->Zg.p;
         double* X = (double*)c->Xp.p;
@@ -929,16 +975,20 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         int nsb[2] = {0, 0};
         long long poff = 0;
         for (int b = 0; b < 2; ++b) {
-          const long long mb = gz_mb[j][b], Kb = gz_Kb[j][kind][b];
+          const long long mb = gz_mb[j][b];
+          long long Kb = gz_Kb[j][kind][b];
+          const long long r0 = b == 0 ? 0 : gz_mb[j][0];
+          long long k0 = b == 0 ? 0 : gz_Kb[j][kind][0];
+          if (phase == PH_ENV) {
+            long long lo = 0;
+            Kb = kpart(Kb, &lo);
+            k0 += lo;
+          }
           if (mb == 0 || Kb == 0) continue;
-          const long long r0 = b == 0 ? 0 : gz_mb[j][0], k0 = b == 0 ? 0 : gz_Kb[j][kind][0];
           const int nsplit = gram_splits(mb, Kb);
           double* pdst = (double*)c->parts.p + poff;
-          launch_gemm_nt_f64(X + r0 * K + k0, K, X + r0 * K + k0, K, pdst, mb, mb * mb, (int)mb, (int)mb,
-                             Kb, nsplit, 1, s);
-          long long kchunk = (Kb + nsplit - 1) / nsplit;
-          kchunk = (kchunk + 15) / 16 * 16;
-          nsb[b] = (int)((Kb + kchunk - 1) / kchunk);
+          nsb[b] = launch_gemm_nt_f64(X + r0 * K + k0, K, X + r0 * K + k0, K, pdst, mb, mb * mb, (int)mb,
+                                      (int)mb, Kb, nsplit, 1, s);
           pb[b] = pdst;
           poff += (long long)nsb[b] * mb * mb;
         }
@@ -948,19 +998,43 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         continue;
       }
       launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
-      const int nsplit = gram_splits(m, K);
-      launch_gemm_nt_f64((const double*)c->Xp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p,
-                         m, m * m, (int)m, (int)m, K, nsplit, 1, s);
-      // the GEMM may round nsplit down; recompute the same way
-      long long kchunk = (K + nsplit - 1) / nsplit;
-      kchunk = (kchunk + 15) / 16 * 16;
-      int used = (int)((K + kchunk - 1) / kchunk);
+      long long k_lo = 0, Kp = K;
+      if (phase == PH_ENV) Kp = kpart(K, &k_lo);
+      if (Kp == 0) {
+        cudaMemsetAsync(Sdst, 0, sizeof(double) * m * m, s);
+        continue;
+      }
+      const int nsplit = gram_splits(m, Kp);
+      // the GEMM may round nsplit down: reduce the partials it wrote
+      const double* X0 = (const double*)c->Xp.p + k_lo;
+      const int used = launch_gemm_nt_f64(X0, K, X0, K, (double*)c->parts.p, m, m * m, (int)m, (int)m, Kp,
+                                          nsplit, 1, s);
       launch_reduce_sym((const double*)c->parts.p, used, (int)m, Sdst, s);
     }
     double* S0 = (double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
+    if (phase == PH_ENV || phase == PH_ISO) {
+      // out: this rank's partial Grams; in: the Grams summed over the ranks
+      const long long mm = m * m;
+      long long off = 0;
+      for (int q = 1; q < j; ++q) off += 4LL * chij[q] * chi_c * chij[q] * chi_c;
+      for (int kind = 0; kind < 4; ++kind) {
+        double* Sk = S0 + kind * mmax * mmax;
+        const cudaError_t ce =
+            phase == PH_ENV
+                ? cudaMemcpyAsync(sh.out + off + kind * mm, Sk, sizeof(double) * mm, cudaMemcpyDefault, s)
+                : cudaMemcpyAsync(Sk, sh.in + off + kind * mm, sizeof(double) * mm, cudaMemcpyDefault, s);
+        if (ce != cudaSuccess) return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+      }
+      if (phase == PH_ENV) continue;
+    }
     launch_assemble_a(S0, S0 + mmax * mmax, chij[j], chi_c, (double*)c->Amat.p + mat_elem_off[2 * j], s);
     launch_assemble_a(S0 + 2 * mmax * mmax, S0 + 3 * mmax * mmax, chij[j], chi_c,
                       (double*)c->Amat.p + mat_elem_off[2 * j + 1], s);
+  }
+  if (phase == PH_ENV) {
+    if (pending_error(c, "the environments") != HOTRG_OK) return HOTRG_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_status(c);
+    return cuda_status(c);
   }
 
   if (pending_error(c, "the environments") != HOTRG_OK) return HOTRG_ECUDA;
@@ -997,7 +1071,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     return launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p, sweeps_out,
                          (DevState*)c->state.p, s);
   };
-  if (!z2g) {
+  if (!env_phase) {
+    // PH_CONTRACT / PH_FINISH: the isometries were installed by PH_ISO
+  } else if (!z2g) {
     for (int g = 0; g < ngrp; ++g) {
       Phase ph(c, 2);
       int cnt = 0;
@@ -1102,7 +1178,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     rank_total += (long long)chij[j] * chij[j];
   }
   if (tangent) CHECK_ALLOC(dev_alloc(c, c->rank, sizeof(int) * rank_total));
-  for (int j = 1; j < d; ++j) {
+  for (int j = 1; j < d && env_phase; ++j) {
     Phase ph(c, 3);
     int n = chij[j] * chij[j];
     // select_kernel addresses matrices 2*leg_index, 2*leg_index+1 from a base
@@ -1119,7 +1195,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   // (parities are tracked while known, and used when the block form is enabled)
   bool z2 = false, track = false;
   std::vector<unsigned char> newpar[kMaxD];
-  if (c->z2_valid) {
+  if (!env_phase) {
+    z2 = c->shard_z2 != 0;
+    track = c->shard_track != 0;
+    for (int j = 1; j < d; ++j) newpar[j] = c->shard_par[j];
+  } else if (c->z2_valid) {
     std::vector<double> hu((size_t)u_total);
     if (cudaMemcpyAsync(hu.data(), c->U64.p, sizeof(double) * u_total, cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
@@ -1154,6 +1234,18 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   }
 
   if (pending_error(c, "the parity read-back") != HOTRG_OK) return HOTRG_ECUDA;
+  if (phase == PH_ISO) {
+    // the isometries of this step stay in the context for PH_CONTRACT and PH_FINISH
+    c->shard_z2 = z2 ? 1 : 0;
+    c->shard_track = track ? 1 : 0;
+    for (int j = 1; j < d; ++j) c->shard_par[j] = newpar[j];
+    c->shard_axis = axis;
+    c->shard_chi = chi;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_status(c);
+    const int r = cuda_status(c);
+    if (r == HOTRG_OK) c->shard_ready = 1;
+    return r;
+  }
   // ---- d/d beta of the chosen environments and of the kept eigenvectors
   // dS = dX X^T + X dX^T (Sec. 3.2), dA = sum dS^ S~ + S^ dS~ (Sec. 4.2.4), and
   // du_k = sum_{l discarded} v_l (v_l . dA u_k) / (lam_k - lam_l) (Sec. 4.2.5)
@@ -1199,11 +1291,8 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
             const long long r0 = b == 0 ? 0 : gz_mb[j][0], q0 = b == 0 ? 0 : gz_Kb[j][kind][0];
             const int nsplit = gram_splits(mb, Kb);
             double* pdst = (double*)c->parts.p + poff;
-            launch_gemm_nt_f64(dX + r0 * K + q0, K, X + r0 * K + q0, K, pdst, mb, mb * mb, (int)mb, (int)mb, Kb,
-                               nsplit, 0, s);
-            long long kchunk = (Kb + nsplit - 1) / nsplit;
-            kchunk = (kchunk + 15) / 16 * 16;
-            nsb[b] = (int)((Kb + kchunk - 1) / kchunk);
+            nsb[b] = launch_gemm_nt_f64(dX + r0 * K + q0, K, X + r0 * K + q0, K, pdst, mb, mb * mb, (int)mb,
+                                        (int)mb, Kb, nsplit, 0, s);
             pb[b] = pdst;
             poff += (long long)nsb[b] * mb * mb;
           }
@@ -1215,11 +1304,8 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         launch_permute(Tc, (double*)c->Xp.p, nd, size, ist, 1.0, s);
         launch_permute((const double*)c->dT.p, (double*)c->dXp.p, nd, size, ist, 1.0, s);
         const int nsplit = gram_splits(m, K);
-        launch_gemm_nt_f64((const double*)c->dXp.p, K, (const double*)c->Xp.p, K, (double*)c->parts.p, m, m * m,
-                           (int)m, (int)m, K, nsplit, 0, s);
-        long long kchunk = (K + nsplit - 1) / nsplit;
-        kchunk = (kchunk + 15) / 16 * 16;
-        const int used = (int)((K + kchunk - 1) / kchunk);
+        const int used = launch_gemm_nt_f64((const double*)c->dXp.p, K, (const double*)c->Xp.p, K,
+                                            (double*)c->parts.p, m, m * m, (int)m, (int)m, K, nsplit, 0, s);
         launch_sym_sum((const double*)c->parts.p, used, (int)m, dS0 + kind * mmax * mmax, s);
       }
       const double* S0 = (const double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
@@ -1245,6 +1331,31 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     if (pending_error(c, "the derivative of the isometries") != HOTRG_OK) return HOTRG_ECUDA;
   }
   // ---- new tensor (Sec. 4.2.9), one c'-slice at a time
+  double bn_done = 0.0;
+  CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
+  double* Tn = (double*)c->T2.p;
+  // derivative of the new tensor: the terms through dU^(1) of the last non-prime
+  // stage land in dTn2 and are added at the end
+  double* dTn = nullptr;
+  double* dTn2 = nullptr;
+  if (tangent) {
+    CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * Rn * Rn));
+    CHECK_ALLOC(dev_alloc(c, c->dTb, sizeof(double) * Rn * Rn));
+    dTn = (double*)c->dT2.p;
+    dTn2 = (double*)c->dTb.p;
+  }
+  // the c'-slices this call contracts (all of them but in PH_CONTRACT)
+  const int sl_lo = phase == PH_CONTRACT ? sh.c_lo : 0;
+  const int sl_hi = phase == PH_CONTRACT ? sh.c_hi : chi_c;
+  const long long slice_elems = Rn * Pn;   // one c'-slice of T': Rn rows x Pn columns (n')
+  if (phase == PH_CONTRACT) {
+    if (sh.n_out) *sh.n_out = (long long)std::max(0, sl_hi - sl_lo) * slice_elems;
+    if (sl_lo < 0 || sl_hi > chi_c || sl_lo >= sl_hi || !sh.out ||
+        sh.cap < (long long)(sl_hi - sl_lo) * slice_elems)
+      return HOTRG_EINVAL;
+  }
+  if (phase == PH_FINISH && (!sh.in || sh.cap != (long long)chi_c * slice_elems)) return HOTRG_EINVAL;
+  if (phase == PH_FULL || phase == PH_CONTRACT) {
   const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
   const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
   const long long Kpad = fp64 ? R : (R + 63) / 64 * 64;
@@ -1297,7 +1408,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   // slots with the same parities, so one list per parity b serves as the row map
   // (first R_b entries) and, padded with -1 to Kp_b, as the K map of block b.
   long long Rb[2] = {0, 0}, Kpb[2] = {0, 0}, maxL = 0;
-  long long moff_rowblk = 0, moff_rowpos = 0, moff_k[2] = {0, 0};
+  long long moff_rowblk = 0, moff_rowpos = 0, moff_kcat = 0, moff_k[2] = {0, 0};
   struct Z2Chunk {
     long long off_blk, off_pos, off_list[2], L[2];
   };
@@ -1323,8 +1434,15 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       rowpos[r] = (int)kmap[p_].size();
       kmap[p_].push_back((int)r);
     }
+    for (int b = 0; b < 2; ++b) Rb[b] = (long long)kmap[b].size();
+    {
+      // the contracted index (rho, n^') runs over the same slots as the rows: both K
+      // lists back to back (parity 0, then parity 1), without padding
+      std::vector<int> kcat(kmap[0].begin(), kmap[0].end());
+      kcat.insert(kcat.end(), kmap[1].begin(), kmap[1].end());
+      moff_kcat = push(kcat);
+    }
     for (int b = 0; b < 2; ++b) {
-      Rb[b] = (long long)kmap[b].size();
       Kpb[b] = fp64 ? Rb[b] : (Rb[b] + 63) / 64 * 64;
       kmap[b].resize(Kpb[b], -1);
     }
@@ -1379,9 +1497,9 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
   }
   const int* zmap = (const int*)c->Zmap.p;
-  // the first non-prime stage reads the product's Z2 blocks directly (no dense C); the
-  // prime chain still writes a dense B, which is gathered into blocks: written in block
-  // order its stores land in partial sectors and the stage ran at half speed
+  // split form with Z2 blocks: the last prime stage writes the B blocks directly (no
+  // dense B, no gather) and the first non-prime stage reads the product's blocks
+  // directly (no dense C)
   const bool zfold = z2 && !fp64 && !c->f64_chains;
   const long long ldz = (maxL + 3) / 4 * 4;   // row pitch of the C blocks
   if (fp64) {
@@ -1403,9 +1521,11 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
                            za + Rb[0] * Kpb[0], s);
     }
   } else {
-    CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
-    if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
-    if (!zfold) CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
+    if (!zfold) {   // with the Z2 blocks the last prime stage writes the B blocks directly
+      CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
+      CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
+    }
     if (tangent) {
       CHECK_ALLOC(dev_alloc(c, c->dBp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
       if (Kpad != R) cudaMemsetAsync(c->dBp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
@@ -1434,23 +1554,6 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         launch_split_bf16((const double*)c->dT.p, R, R, R, (__nv_bfloat16*)c->dAp.p, Kpad, R * Kpad, npieces, s);
       }
     }
-  }
-  double bn_done = 0.0;
-  // The compacted K of a Z2 block holds no exact zeros, while half of the dense K
-  // products are zero: half the chunk keeps the same number of truncating
-  // accumulations per chunk as the dense form.
-  const int zchunk = std::max(1, tc_chunk_kblocks() / 2);
-  CHECK_ALLOC(dev_alloc(c, c->T2, sizeof(double) * Rn * Rn));
-  double* Tn = (double*)c->T2.p;
-  // derivative of the new tensor: the terms through dU^(1) of the last non-prime
-  // stage land in dTn2 and are added at the end
-  double* dTn = nullptr;
-  double* dTn2 = nullptr;
-  if (tangent) {
-    CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * Rn * Rn));
-    CHECK_ALLOC(dev_alloc(c, c->dTb, sizeof(double) * Rn * Rn));
-    dTn = (double*)c->dT2.p;
-    dTn2 = (double*)c->dTb.p;
   }
   auto view_elems = [](const View& v) {
     long long n_ = 1;
@@ -1482,7 +1585,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
   }
 
   const void* cblk_cur[2] = {nullptr, nullptr};   // this sub-slice's C blocks (Z2)
-  for (int sl = 0; sl < chi_c; ++sl)
+  for (int sl = sl_lo; sl < sl_hi; ++sl)
   for (int n1lo = 0; n1lo < nnew1; n1lo += n1_chunk) {
     const int n1cnt = std::min(n1_chunk, nnew1 - n1lo);
     const long long Nc = (long long)n1cnt * (Ns / nnew1);   // bottleneck columns of this sub-slice
@@ -1539,6 +1642,49 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         cd.piece_stride = Nc * Kpad;
         launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j] + ucol, dst,
                             last ? OUT_BF16_SPLIT : OUT_F64, s);
+      } else if (last && zfold) {
+        // straight into the Z2 blocks of B: the outputs whose column parity matches
+        // the parity of their k, at the positions the bottleneck's blocks use
+        cd.npieces = npieces;
+        const Z2Chunk& ch = zch[n1lo / n1_chunk];
+        const int q = c->par[to[0]][sl];
+        Z2Out zo;
+        zo.kcat = zmap + moff_kcat;
+        zo.R = (unsigned)R;
+        zo.rb0 = (unsigned)Rb[0];
+        zo.cblk = zmap + ch.off_blk;
+        zo.cpos = zmap + ch.off_pos;
+        zo.q = q;
+        zo.kpad = Kpad;
+        zo.nrow_step = cd.n_out_stride / Kpad;
+        for (int b = 0; b < 2; ++b) {
+          const long long Nb = ch.L[b ^ q];
+          __nv_bfloat16* zb = (__nv_bfloat16*)c->Zb.p + npieces * (b == 0 ? 0 : maxL * Kpb[0]);
+          zo.blk[b] = zb;
+          zo.ld[b] = Kpb[b];
+          zo.pstride[b] = Nb * Kpb[b];
+          // the K padding of every row (of every piece) reads as zero
+          if (Kpb[b] > Rb[b] && Nb > 0 &&
+              cudaMemset2DAsync(zb + Rb[b], sizeof(__nv_bfloat16) * Kpb[b], 0,
+                                sizeof(__nv_bfloat16) * (Kpb[b] - Rb[b]), (size_t)npieces * Nb, s) !=
+                  cudaSuccess)
+            return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+        }
+        {
+          // the leading free dims of the stage must be exactly the k dims (R values),
+          // the others rows of the dense view (strides multiples of Kpad)
+          long long kprod = 1;
+          int q0 = 0;
+          while (q0 < cd.ndim && cd.out_stride[q0] < Kpad) kprod *= cd.size[q0++];
+          bool okz = kprod == R && cd.n_out_stride % Kpad == 0;
+          for (int q1 = q0; q1 < cd.ndim; ++q1) okz = okz && cd.out_stride[q1] % Kpad == 0;
+          for (int q1 = 0; q1 + 1 < cd.ndim; ++q1) okz = okz && cd.out_stride[q1] <= cd.out_stride[q1 + 1];
+          if (!okz) {
+            c->poisoned = HOTRG_EINVAL;
+            return HOTRG_EINVAL;
+          }
+        }
+        launch_chain_f32_z2out(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, zo, s);
       } else {
         cd.npieces = npieces;
         cd.piece_stride = Nc * Kpad;
@@ -1606,7 +1752,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
         } else {
           __nv_bfloat16* zb = (__nv_bfloat16*)c->Zb.p + npieces * b_off;
           float* zc = (float*)c->Zc.p + c_off;
-          {
+          if (!zfold) {   // else the last prime stage wrote the block
             Phase pg(c, 11);
             launch_z2_gather_bf16((const __nv_bfloat16*)c->Bp.p, Kpad, Nc * Kpad, nmap, (int)Nb, kmap,
                                   (int)Kpb[b], zb, Nb * Kpb[b], npieces, s);
@@ -1614,7 +1760,7 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
           Phase ph(c, 6);
           if (launch_tc_gemm((const __nv_bfloat16*)c->Za.p + npieces * a_off, (int)Rb[b], zb, (int)Nb,
                              (int)Kpb[b], npieces, nterms, terms_a, terms_b, zc, ldz,
-                             &((DevState*)c->state.p)->status, s, nullptr, zchunk) != 0)
+                             &((DevState*)c->state.p)->status, s, nullptr) != 0)
             return launch_failed(c, "tensor-core GEMM (Z2 block)", Rb[b], Nb, Kpb[b]);
           cblk[b] = zc;
         }
@@ -1740,6 +1886,29 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
       cin = out;
     }
   }
+  }   // PH_FULL, PH_CONTRACT: the contraction
+
+  if (phase == PH_CONTRACT) {
+    // out: slice c' of T' (columns c' Pn .. of every row) at (c' - c_lo) Rn Pn, row-major
+    if (pending_error(c, "the non-prime chain") != HOTRG_OK) return HOTRG_ECUDA;
+    for (int sl = sl_lo; sl < sl_hi; ++sl)
+      if (cudaMemcpy2DAsync(sh.out + (long long)(sl - sl_lo) * slice_elems, sizeof(double) * Pn,
+                            Tn + (long long)sl * Pn, sizeof(double) * Rn, sizeof(double) * Pn, Rn,
+                            cudaMemcpyDefault, s) != cudaSuccess)
+        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    c->shard_bn_done = bn_done;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_status(c);
+    return cuda_status(c);
+  }
+  if (phase == PH_FINISH) {
+    // in: every slice, gathered over the ranks, in the layout PH_CONTRACT writes
+    for (int sl = 0; sl < chi_c; ++sl)
+      if (cudaMemcpy2DAsync(Tn + (long long)sl * Pn, sizeof(double) * Rn, sh.in + (long long)sl * slice_elems,
+                            sizeof(double) * Pn, sizeof(double) * Pn, Rn, cudaMemcpyDefault, s) != cudaSuccess)
+        return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
+    bn_done = c->shard_bn_done;   // this rank's share of the bottleneck
+    c->shard_ready = 0;
+  }
 
   if (pending_error(c, "the non-prime chain") != HOTRG_OK) return HOTRG_ECUDA;
   if (tangent) launch_axpby(1.0, dTn2, 1.0, dTn, Rn * Rn, s);
@@ -1772,6 +1941,49 @@ int hotrg_step(hotrg_ctx* c, int axis, int chi) {
     c->last_u_off[j - 1] = u_off[j];
   }
   return cuda_status(c);
+}
+
+}  // namespace
+
+int hotrg_shard_env(hotrg_ctx* c, int axis, int chi, int part, int nparts, double* S, int64_t cap,
+                    int64_t* n) {
+  if (nparts < 1 || part < 0 || part >= nparts) return HOTRG_EINVAL;
+  Shard sh;
+  sh.phase = PH_ENV;
+  sh.part = part;
+  sh.nparts = nparts;
+  sh.out = S;
+  sh.cap = cap;
+  sh.n_out = n;
+  return step_impl(c, axis, chi, sh);
+}
+
+int hotrg_shard_isometries(hotrg_ctx* c, int axis, int chi, const double* S, int64_t n) {
+  Shard sh;
+  sh.phase = PH_ISO;
+  sh.in = S;
+  sh.cap = n;
+  return step_impl(c, axis, chi, sh);
+}
+
+int hotrg_shard_contract(hotrg_ctx* c, int axis, int chi, int c_lo, int c_hi, double* slices, int64_t cap,
+                         int64_t* n) {
+  Shard sh;
+  sh.phase = PH_CONTRACT;
+  sh.c_lo = c_lo;
+  sh.c_hi = c_hi;
+  sh.out = slices;
+  sh.cap = cap;
+  sh.n_out = n;
+  return step_impl(c, axis, chi, sh);
+}
+
+int hotrg_shard_finish(hotrg_ctx* c, int axis, int chi, const double* slices, int64_t n) {
+  Shard sh;
+  sh.phase = PH_FINISH;
+  sh.in = slices;
+  sh.cap = n;
+  return step_impl(c, axis, chi, sh);
 }
 
 static int find_leg(hotrg_ctx* c, int leg) {
@@ -2138,6 +2350,25 @@ int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int*
   if (n) *n = 12;
   if (contraction_fp64) *contraction_fp64 = c->last_fp64;
   return HOTRG_OK;
+}
+
+int hotrg_gemm_rate(int mode, int M, int N, int K, int iters, double* ms_per_launch) {
+  if ((mode != HOTRG_PREC_BF16X3 && mode != HOTRG_PREC_BF16X6) || M < 1 || N < 1 || K < 1 || M > (1 << 20) ||
+      N > (1 << 20) || K > (1 << 20) || iters < 1 || !ms_per_launch)
+    return HOTRG_EINVAL;
+  if (!tc_gemm_ready()) return HOTRG_ECUDA;
+  const int r = measure_tc_gemm_rate(mode == HOTRG_PREC_BF16X3 ? 2 : 3, M, N, (K + 63) / 64 * 64, iters,
+                                     ms_per_launch);
+  if (r == -1) return HOTRG_EINVAL;
+  if (r == -2) return HOTRG_ENOMEM;
+  if (r == -3) return HOTRG_ECUDA;
+  return r;
+}
+
+int hotrg_fp64_rate(double* tflops) {
+  if (!tflops) return HOTRG_EINVAL;
+  const int r = measure_fp64_rate(tflops);
+  return r == 0 ? HOTRG_OK : (r == -2 ? HOTRG_ENOMEM : HOTRG_ECUDA);
 }
 
 int hotrg_device_bytes(hotrg_ctx* c, size_t* bytes) {

@@ -10,6 +10,7 @@
 namespace hotrg {
 
 constexpr int kMaxD = 4;
+constexpr int kMaxDevices = 64;  // per-device caches (SM counts, kernel attributes)
 constexpr int kMaxDims = 10;     // tensor ranks handled by the index kernels
 constexpr int kMaxBond = 64;
 
@@ -79,9 +80,12 @@ void launch_finish_step(double* Y, int chi_c, DevState* st, int p, int first, cu
 void launch_scale(const double* in, double* out, long long n, const DevState* st, cudaStream_t s);
 
 // ---- kernels_env.cu
-void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb,
-                        double* C, long long ldc, long long split_stride,
-                        int M, int N, long long K, int nsplit, int upper_only, cudaStream_t s);
+// FP64 FMA rate of the current device in TFLOP/s (CUDA events; 0 or a negative status)
+int measure_fp64_rate(double* tflops);
+// returns the number of split-K partials written
+int launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb,
+                       double* C, long long ldc, long long split_stride,
+                       int M, int N, long long K, int nsplit, int upper_only, cudaStream_t s);
 void launch_reduce_sym(const double* parts, int nsplit, int m, double* G, cudaStream_t s);
 void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int chi_c,
                        double* A, cudaStream_t s);
@@ -110,7 +114,29 @@ void launch_chain_f64(const ChainDesc& d, const double* in, const double* U, dou
                       cudaStream_t s);
 void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, const double* U,
                          void* out, int out_mode, cudaStream_t s);
-enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2 };
+enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2, OUT_Z2_SPLIT = 3 };
+
+// Last prime stage written straight into the Z2 blocks of the bottleneck's B operand.
+// The stage's out view is the dense B (row (n', n~) x kpad + k, k = (rho, n^')), whose
+// leading free dims are exactly the k dims (R values).  Threads run over the K lists of
+// both parities concatenated (kcat: dense k of list position x; block 0 = the first rb0
+// positions), so the lanes of a warp hold consecutive positions of one block row.  An
+// output goes to block b = parity(k) if its row's parity p_N satisfies p_N ^ q == b
+// (the other half meets only zero blocks of T and is not formed), at row cpos[row] and
+// column = the position of k in its list; split into BF16 pieces.
+struct Z2Out {
+  const int* kcat;        // dense k of every position of the two K lists (R entries)
+  unsigned R;             // entries of kcat (product of the k dims)
+  unsigned rb0;           // length of the parity-0 list
+  const int* cblk;        // per column (n', n~) of this sub-slice: parity p_N
+  const int* cpos;        // per column: position in the list of its parity
+  int q;                  // parity of the c'-slice
+  __nv_bfloat16* blk[2];  // the blocks
+  long long ld[2];        // row pitch of block b (Kp_b)
+  long long pstride[2];   // piece stride of block b
+  long long kpad;         // row pitch of the dense out view
+  long long nrow_step;    // rows between consecutive values of the stage's new index
+};
 
 // First non-prime stage read straight from the Z2 blocks of the bottleneck's product C.
 // The stage's in strides are packed: (C row stride) << 32 | (C column stride).
@@ -125,6 +151,8 @@ struct Z2In {
 };
 void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, int out_mode,
                            cudaStream_t s);
+void launch_chain_f32_z2out(const ChainDesc& d, const void* in, int in_is_f64, const float* U, const Z2Out& zo,
+                            cudaStream_t s);
 
 // ---- kernels_z2.cu
 struct Z2Slots {
@@ -165,14 +193,17 @@ void launch_z2_scatter_f64(const double* c0, long long ld0, const double* c1, lo
                            int q, int nrows, int ncols, double* dense, cudaStream_t s);
 
 // ---- kernels_tc_gemm.cu
-// C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T;
-// chunk_kblocks: accumulation chunk of the leading terms in K-blocks (0: the default)
+// C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T,
+// Kpad a multiple of 32, accumulated in chunks of 32 along K
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb,
-                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out,
-                   int chunk_kblocks = 0);
+                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out);
 int tc_gemm_ready();
-int tc_chunk_kblocks();
+// milliseconds per launch of the split-BF16 GEMM on device-resident operands (rate probe)
+int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch);
+
+// ---- kernels_tensor.cu: streaming multiprocessors of the current device (cached per device)
+int sm_count();
 
 extern std::atomic<long long> g_launches;   // kernels launched by this library
 // ---- kernels_tangent.cu (d/d beta in forward mode)

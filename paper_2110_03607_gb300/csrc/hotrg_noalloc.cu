@@ -13,7 +13,6 @@ namespace hotrg {
 namespace {
 
 constexpr size_t kScratchBytes = size_t(64) << 20;  // HOTRG_NOALLOC_SCRATCH_BYTES
-constexpr int kMaxDevices = 64;
 
 // Every GPU that loads the library holds this array until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -59,7 +58,9 @@ using namespace hotrg;
 
 extern "C" int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double* A, const double* B,
                                      double* C, void* stream) {
-  if (mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6 || M < 1 || N < 1 || K < 1 || !A || !B || !C)
+  // the size limits of hotrg_gemm_nt, so that bad sizes give HOTRG_EINVAL in every mode
+  if (mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6 || M < 1 || N < 1 || K < 1 || M > (1 << 20) ||
+      N > (1 << 20) || K > (1 << 20) || !A || !B || !C)
     return HOTRG_EINVAL;
   if ((long long)M * K > (1LL << 31) || (long long)N * K > (1LL << 31) || (long long)M * N > (1LL << 31))
     return HOTRG_EINVAL;
@@ -104,7 +105,8 @@ extern "C" int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double
     if (status == HOTRG_OK) {
       long long n = (long long)M * N;
       long long blocks = (n + 255) / 256;
-      if (blocks > 152 * 16) blocks = 152 * 16;
+      const long long cap = 16LL * sm_count();
+      if (blocks > cap) blocks = cap;
       widen_kernel<<<(unsigned)blocks, 256, 0, s>>>(c32, C, n);
       ++g_launches;
     }

@@ -43,7 +43,8 @@ struct URow<float, NN> {
 
 template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
 __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
-                                                    const TAcc* __restrict__ U, void* out, Z2In zi) {
+                                                    const TAcc* __restrict__ U, void* out, Z2In zi,
+                                                    Z2Out zo) {
   extern __shared__ __align__(16) unsigned char smem_u[];
   TAcc* us = reinterpret_cast<TAcc*>(smem_u);
   const int rows = d.chi * d.chi;
@@ -56,6 +57,13 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.total; t += stride) {
     unsigned rem = (unsigned)t;
+    unsigned kidx = 0;
+    if (OUT == OUT_Z2_SPLIT) {
+      // t = (row group, list position): the thread's dense k comes from the K lists
+      const unsigned grp = rem / zo.R;
+      kidx = rem - grp * zo.R;
+      rem = grp * zo.R + (unsigned)zo.kcat[kidx];
+    }
     long long in_off = 0, out_off = 0;
     int a_val = 0;
 #pragma unroll
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
 #pragma unroll
       for (int n = 0; n < NN; ++n)
         if (n < d.nn) o[out_off + n * d.n_out_stride] = (double)acc[n];
-    } else {
+    } else if (OUT == OUT_BF16_SPLIT) {
       __nv_bfloat16* o = (__nv_bfloat16*)out;
 #pragma unroll
       for (int n = 0; n < NN; ++n) {
@@ -170,21 +178,43 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
           x -= (TAcc)__bfloat162float(bv);
         }
       }
+    } else {
+      // OUT_Z2_SPLIT: consecutive threads hold consecutive positions of one K list, so
+      // a warp's stores to a block row are contiguous
+      const long long row0 = out_off / zo.kpad;
+      const int kb = kidx >= zo.rb0 ? 1 : 0;
+      const long long kpos = (long long)(kb ? kidx - zo.rb0 : kidx);
+      __nv_bfloat16* ob = zo.blk[kb] + kpos;
+      const long long ld = zo.ld[kb], ps = zo.pstride[kb];
+#pragma unroll
+      for (int n = 0; n < NN; ++n) {
+        if (n >= d.nn) break;
+        const long long row = row0 + n * zo.nrow_step;
+        if ((zo.cblk[row] ^ zo.q) != kb) continue;
+        __nv_bfloat16* o = ob + (long long)zo.cpos[row] * ld;
+        TAcc x = acc[n];
+        for (int p = 0; p < d.npieces; ++p) {
+          __nv_bfloat16 bv = to_bf16(x);
+          o[p * ps] = bv;
+          x -= (TAcc)__bfloat162float(bv);
+        }
+      }
     }
   }
 }
 
 template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
 static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, cudaStream_t s,
-                       const Z2In& zi = Z2In{}) {
+                       const Z2In& zi = Z2In{}, const Z2Out& zo = Z2Out{}) {
   size_t smem = (size_t)d.chi * d.chi * URow<TAcc, NN>::ld * sizeof(TAcc);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT, ZIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   long long blocks = (d.total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const long long cap = 16LL * sm_count();
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  chain_kernel<TIn, TAcc, NN, OUT, ZIN><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi);
+  chain_kernel<TIn, TAcc, NN, OUT, ZIN><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi, zo);
   ++g_launches;
 }
 
@@ -220,6 +250,22 @@ void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, v
                            cudaStream_t s) {
   if (out_mode == OUT_F64) dispatch_nn_z2in<OUT_F64>(d, zi, U, out, s);
   else dispatch_nn_z2in<OUT_F32>(d, zi, U, out, s);
+}
+
+template <typename TIn>
+static void dispatch_nn_z2out(const ChainDesc& d, const TIn* in, const float* U, const Z2Out& zo, cudaStream_t s) {
+  const Z2In none{};
+  if (d.nn <= 4) launch_one<TIn, float, 4, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 8) launch_one<TIn, float, 8, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 16) launch_one<TIn, float, 16, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 24) launch_one<TIn, float, 24, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+  else launch_one<TIn, float, 32, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+}
+
+void launch_chain_f32_z2out(const ChainDesc& d, const void* in, int in_is_f64, const float* U, const Z2Out& zo,
+                            cudaStream_t s) {
+  if (in_is_f64) dispatch_nn_z2out<double>(d, (const double*)in, U, zo, s);
+  else dispatch_nn_z2out<float>(d, (const float*)in, U, zo, s);
 }
 
 void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U, void* out,

@@ -140,15 +140,21 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
 template <int NPL>
 static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
                            int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
-  // SM count and resident CTAs per SM, queried once (thread-safe static initialisation)
-  static const int2 occ = [] {
-    int dev = 0, sms = 0, per = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_onesided_kernel<NPL>, 256, 0);
-    return make_int2(sms, per < 1 ? 1 : per);
-  }();
-  const int s_sms = occ.x, s_per_sm = occ.y;
+  // resident CTAs per SM, queried once per device
+  static std::atomic<int> per_cache[kMaxDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per = (dev >= 0 && dev < kMaxDevices) ? per_cache[dev].load(std::memory_order_relaxed) : 0;
+  if (per < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_onesided_kernel<NPL>, 256, 0) !=
+            cudaSuccess ||
+        per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    if (dev >= 0 && dev < kMaxDevices) per_cache[dev].store(per, std::memory_order_relaxed);
+  }
+  const int s_sms = sm_count(), s_per_sm = per;
   int mp = n + (n & 1);
   int tasks = nmat * (mp / 2);
   // one block per SM (up to the task count): tasks are dealt round-robin over blocks
@@ -285,11 +291,105 @@ __global__ void __launch_bounds__(1024) jacobi32_block_kernel(const double* __re
   }
 }
 
+// FP32 warm start for n <= 170: one CTA per matrix holds all of W and V in shared
+// memory (2 n^2 floats) and runs the round-robin sweeps of one-sided Jacobi with a
+// __syncthreads between rounds -- no grid barrier.  Same rotation test and stopping
+// rule as the block version below.
+template <int NPL>
+__global__ void __launch_bounds__(1024, 1) jacobi32_smem_kernel(const double* __restrict__ A, float* W, float* V,
+                                                                int n, int max_sweeps) {
+  extern __shared__ float jsm[];
+  __shared__ int s_rot;
+  const long long nn = (long long)n * n;
+  float* sw = jsm;
+  float* sv = jsm + nn;
+  const double* Am = A + blockIdx.x * nn;
+  for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+    sw[e] = (float)Am[e];                       // A symmetric: row i = column i
+    sv[e] = (e / n == e % n) ? 1.0f : 0.0f;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int mp = n + (n & 1), npairs = mp / 2, rounds = mp - 1;
+  const float tol = 4.0f * (float)n * 1.1920929e-7f;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < rounds; ++r) {
+      for (int k = warp; k < npairs; k += nw) {
+        int p = rr_slot(k, r, mp), q = rr_slot(mp - 1 - k, r, mp);
+        if (p >= n || q >= n) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        float* wp = sw + (long long)p * n;
+        float* wq = sw + (long long)q * n;
+        float xs[NPL], ys[NPL];
+        float a = 0.f, bb = 0.f, g = 0.f;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          float x = i < n ? wp[i] : 0.f, y = i < n ? wq[i] : 0.f;
+          xs[u] = x;
+          ys[u] = y;
+          a = fmaf(x, x, a);
+          bb = fmaf(y, y, bb);
+          g = fmaf(x, y, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (g == 0.f || !(fabsf(g) > tol * sqrtf(a * bb))) continue;
+        float zeta = (bb - a) / (2.f * g);
+        float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
+        float* vp = sv + (long long)p * n;
+        float* vq = sv + (long long)q * n;
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          int i = lane + 32 * u;
+          if (i < n) {
+            wp[i] = c * xs[u] - sn * ys[u];
+            wq[i] = sn * xs[u] + c * ys[u];
+            float x = vp[i], y = vq[i];
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (rot == 0) break;
+  }
+  float* Wm = W + blockIdx.x * nn;
+  float* Vm = V + blockIdx.x * nn;
+  for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+    Wm[e] = sw[e];
+    Vm[e] = sv[e];
+  }
+}
+
 // Block size b: four blocks (three outer rounds, one grid barrier each, per sweep) when
 // two blocks of W and V fit in 200 KB of shared memory, else b = 32 (or less) and
 // nb = ceil(n / b) rounded up to even.
 int launch_jacobi32_block(const double* A, float* W32, float* V32, int n, int nmat, int max_sweeps,
                           int* counters, cudaStream_t s) {
+  {
+    const size_t smem1 = (size_t)2 * n * n * sizeof(float);
+    const int npl1 = (n + 31) / 32;
+    if (smem1 <= 227 * 1024 && npl1 <= 8) {
+      void* k1 = npl1 <= 2 ? (void*)jacobi32_smem_kernel<2>
+               : npl1 <= 4 ? (void*)jacobi32_smem_kernel<4> : (void*)jacobi32_smem_kernel<8>;
+      if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) != cudaSuccess)
+        return -1;
+      void* args1[] = {&A, &W32, &V32, &n, &max_sweeps};
+      const cudaError_t e1 = cudaLaunchKernel(k1, dim3(nmat), dim3(1024), args1, smem1, s);
+      ++g_launches;
+      return e1 == cudaSuccess ? 0 : -1;
+    }
+  }
   int b = (n + 3) / 4;
   if (b > 64 || (size_t)4 * b * n * sizeof(float) > 200 * 1024) {
     b = 32;

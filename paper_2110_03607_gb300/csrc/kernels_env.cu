@@ -92,9 +92,11 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
   }
 }
 
-void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
-                        long long ldc, long long split_stride, int M, int N, long long K,
-                        int nsplit, int upper_only, cudaStream_t s) {
+// Returns the number of split-K partial products written (nsplit after rounding the
+// K chunk up to a multiple of BK): the partials a reduction must read.
+int launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb, double* C,
+                       long long ldc, long long split_stride, int M, int N, long long K,
+                       int nsplit, int upper_only, cudaStream_t s) {
   if (nsplit < 1) nsplit = 1;
   long long kchunk = (K + nsplit - 1) / nsplit;
   kchunk = (kchunk + BK - 1) / BK * BK;
@@ -106,6 +108,7 @@ void launch_gemm_nt_f64(const double* A, long long lda, const double* B, long lo
   gemm_nt_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, split_stride, M, N, K, kchunk,
                                            upper_only);
   ++g_launches;
+  return nsplit;
 }
 
 // Batched small FP64 products for the Newton-Schulz re-orthonormalisation in the
@@ -240,6 +243,53 @@ void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int 
   if (blocks > 4096) blocks = 4096;
   assemble_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(s_hat, s_chk, chi_j, chi_c, A);
   ++g_launches;
+}
+
+// FP64 FMA throughput probe: every thread runs eight independent chains
+// x <- x * a + b (|a| < 1, so the values stay bounded), `iters` steps each, and
+// writes one sum so that the chains are not removed.  2 flops per FMA.
+__global__ void __launch_bounds__(256) dfma_rate_kernel(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += x[k];
+  if (threadIdx.x == 0) out[blockIdx.x] = sum;
+}
+
+int measure_fp64_rate(double* tflops) {
+  const int sms = sm_count(), blocks = 8 * sms, threads = 256, iters = 1 << 15;
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * blocks) != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 0.0f;
+  for (int rep = 0; rep < 3; ++rep) {   // the first launch warms up (clocks, module load)
+    cudaEventRecord(e0, 0);
+    dfma_rate_kernel<<<blocks, threads>>>(out, iters, 0.9999999, 1e-7);
+    ++g_launches;
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || best <= 0.0f) return -3;
+  *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+  return 0;
 }
 
 }  // namespace hotrg

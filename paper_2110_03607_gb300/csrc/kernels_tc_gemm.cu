@@ -2,23 +2,31 @@
 // tensor cores:
 //   C[(c, n^), (n', n~)] = sum_{(rho, n^')} T[(c, n^), (rho, n^')] B[(n', n~), (rho, n^')]
 // with both operands split into BF16 pieces, x = x_0 + x_1 (+ x_2), and the
-// product formed as a sum of piece products (terms).
+// product formed as a sum of piece products (terms) x_i y_j.
 //
-// One CTA computes a 128 x 256 tile of C.  Warp 8 (one lane) streams 64-wide
-// K slabs of the A and B pieces into a 4-stage shared-memory ring with TMA
-// (128-byte swizzle).  Warp 9 (one lane) issues tcgen05.mma (M=128, N=256,
-// K=16, kind::f16, BF16 x BF16 -> FP32) and releases ring slots with
-// tcgen05.commit.  The tensor core's FP32 accumulation truncates, so a long
-// accumulation drifts towards zero; the K loop is therefore cut into short
-// chunks, each accumulated from zero into one of two TMEM buffers (256
-// columns each, used alternately), while warps 0-7 drain the other buffer
-// with tcgen05.ld (warp w owns TMEM lanes 32(w%4).. and columns 128(w/4)..)
-// and add the chunk into FP32 registers with round-to-nearest.  Every
-// mbarrier wait is bounded in time; an expired wait sets a global error flag
-// that also makes the CTAs still to come exit at once.
+// Persistent kernel: one CTA per SM walks the 128 x 256 tiles of C (tile index
+// blockIdx.x, + gridDim.x, ...; row tiles fastest, so the CTAs running at one time
+// share the B tiles in L2).  Warp 8 (one lane) streams 32-wide K slabs into a
+// 3-stage shared-memory ring with TMA (64-byte swizzle); one stage holds EVERY
+// piece of the A and B slabs (3 x 8 KiB + 3 x 16 KiB), so each piece is loaded
+// once per slab and serves all the terms that use it.  Warp 9 (one lane) issues
+// tcgen05.mma (M=128, N=256, K=16, kind::f16, BF16 x BF16 -> FP32).  The tensor
+// core's FP32 accumulation truncates, so a long accumulation drifts towards zero:
+// the K range is therefore cut into chunks of CHUNK_SLABS slabs, each accumulated
+// from zero in one of two TMEM buffers (256 columns each, used alternately) while
+// warps 0-7 drain the other buffer with tcgen05.ld (warp w owns TMEM lanes
+// 32(w%4).. and columns 128(w/4)..) and add the chunk into FP32 registers with
+// round-to-nearest.  Within a chunk the small terms (order 2^-16, then 2^-8) of
+// all its slabs go first, the leading term x_0 y_0 last: the small terms then
+// truncate at their own (small) scale and only the leading MMAs truncate at the
+// scale of the result.  Every mbarrier wait is bounded in time; an expired wait
+// sets a global error flag that also makes the other CTAs give up.
 #include <cuda.h>
 #include <stdio.h>
 #include <stdlib.h>
+
+#include <algorithm>
+#include <atomic>
 
 #include "hotrg_internal.cuh"
 #include "../../include/hotrg.h"
@@ -26,28 +34,40 @@
 namespace hotrg {
 
 namespace {
-constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
-constexpr int A_STAGE = TM * TK * 2;   // 16 KiB
-constexpr int B_STAGE = TN * TK * 2;   // 32 KiB
+constexpr int TM = 128, TN = 256, TK = 32, STAGES = 3, MAXP = 3;
+constexpr int A_PIECE = TM * TK * 2;                      // 8 KiB
+constexpr int B_PIECE = TN * TK * 2;                      // 16 KiB
+constexpr int STAGE_BYTES = MAXP * (A_PIECE + B_PIECE);   // 72 KiB
 constexpr int TMEM_COLS = 512;         // two 256-column FP32 accumulators
-constexpr int NTHREADS = 320;          // 8 epilogue warps + producer + MMA
-constexpr int SMEM_BYTES = 1024 + STAGES * (A_STAGE + B_STAGE) + 256;
+// Epilogue warps: EPI_WARPS / 4 per TMEM lane quarter, each draining EPI_COLS columns
+#ifndef HOTRG_TC_EPI_WARPS
+#define HOTRG_TC_EPI_WARPS 8
+#endif
+constexpr int EPI_WARPS = HOTRG_TC_EPI_WARPS;
+static_assert(EPI_WARPS == 8 || EPI_WARPS == 16, "8 or 16 epilogue warps");
+constexpr int EPI_COLS = TN / (EPI_WARPS / 4);      // 128 or 64
+constexpr int LD_COLS = EPI_WARPS == 8 ? 32 : 16;   // columns per tcgen05.ld
+constexpr int W_PROD = EPI_WARPS, W_MMA = EPI_WARPS + 1;
+constexpr int NTHREADS = 32 * (EPI_WARPS + 2);      // epilogue warps + producer + MMA
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
 }  // namespace
 
+// K slabs per accumulation chunk (chunk length 32 x this along K)
+#ifndef HOTRG_TC_CHUNK_SLABS
+#define HOTRG_TC_CHUNK_SLABS 2
+#endif
+constexpr int CHUNK_SLABS = HOTRG_TC_CHUNK_SLABS;
+static_assert(CHUNK_SLABS >= 1 && CHUNK_SLABS < STAGES, "a chunk must leave a ring stage to prefetch into");
+
 struct TcTerms {
   int nterms;
-  int pa[9];
-  int pb[9];
-  int clen[9];   // K-blocks per accumulation chunk of each term
+  int nsmall;    // terms [0, nsmall) are of order 2^-8 or smaller, the rest leading
+  int npieces;   // pieces of each operand loaded per K slab
+  // term t: A piece (code >> 4t) & 3, B piece (code >> (4t + 2)) & 3 (kept in a
+  // register: an indexed array would live in local memory on the MMA issuer's path)
+  unsigned long long code;
 };
-
-// chunks of term t: ceil(kblocks / clen[t])
-__device__ __forceinline__ int count_chunks(const TcTerms& terms, int kblocks) {
-  int n = 0;
-  for (int t = 0; t < terms.nterms; ++t) n += (kblocks + terms.clen[t] - 1) / terms.clen[t];
-  return n;
-}
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -112,14 +132,15 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, void* dst, u
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with the 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// with the 64-byte swizzle: rows of 64 bytes (32 BF16 along K), 8-row groups
+// 512 bytes apart (the swizzle pattern repeats every 512 bytes).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
   return d;
 }
 
@@ -153,8 +174,8 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32 columns of FP32 from TMEM; the values are usable after tmem_wait_ld()
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+// 32 lanes x 32 (or 16) columns of FP32 from TMEM; usable after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -166,6 +187,15 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32
         "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
 
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -173,15 +203,12 @@ __device__ __forceinline__ void tmem_wait_ld() {
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   float* __restrict__ C, int M, int N, long long ldc, int kblocks, TcTerms terms,
+                   float* __restrict__ C, int M, int N, long long ldc, int kslabs, TcTerms terms,
                    int* g_err) {
   extern __shared__ uint8_t smem_raw[];
   volatile int* gerr = g_err;
-  if (*gerr) return;  // an earlier CTA gave up: do nothing
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_STAGE;
-  uint64_t* full = (uint64_t*)(sB + STAGES * B_STAGE);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;      // [2] MMA -> epilogue
   uint64_t* tempty = tfull + 2;          // [2] epilogue -> MMA
@@ -190,9 +217,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile int* cta_abort = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-  const int total = terms.nterms * kblocks;
-  const int nchunks = count_chunks(terms, kblocks);
+  const int mtiles = (M + TM - 1) / TM;
+  const long long ntiles = (long long)mtiles * ((N + TN - 1) / TN);
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...; one chunk per K slab
+  const long long tiles_here =
+      ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int np = terms.npieces;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -201,15 +231,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull + b, 1);
-      mbar_init(tempty + b, 8);
+      mbar_init(tempty + b, EPI_WARPS);
     }
     mbar_init(drain, 1);
-    *cta_abort = 0;
+    *cta_abort = *gerr ? 1 : 0;   // an earlier launch or CTA gave up: do nothing
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
   }
-  if (warp == 9) {
+  if (warp == W_MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tmem_slot)),
                  "r"(TMEM_COLS)
@@ -220,74 +250,101 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // read once, after the barrier, so that every thread of the CTA takes the same path
+  const long long my_tiles = *cta_abort ? 0 : tiles_here;
+  const long long total = my_tiles * kslabs;
 
-  if (warp == 8) {
+  if (warp == W_PROD) {
     if (lane == 0) {
-      // ---------------- TMA producer
-      int issued = 0;
+      // ---------------- TMA producer: slab g of this CTA = K slab g % kslabs of
+      // tile blockIdx.x + (g / kslabs) * gridDim.x; all pieces of A and B
+      long long issued = 0;
       bool ok = true;
-      for (int it = 0; it < total; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      for (long long g = 0; g < total; ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
         if (!mbar_wait(empty + s, ph ^ 1u, cta_abort, gerr)) {
           ok = false;
           break;
         }
-        mbar_expect_tx(full + s, A_STAGE + B_STAGE);
-        const int t = it / kblocks, kb = it - t * kblocks;
-        tma_load_3d(&tmA, sA + s * A_STAGE, full + s, kb * TK, m0, terms.pa[t]);
-        tma_load_3d(&tmB, sB + s * B_STAGE, full + s, kb * TK, n0, terms.pb[t]);
-        issued = it + 1;
+        const long long tile = blockIdx.x + (g / kslabs) * gridDim.x;
+        const int kb = (int)(g % kslabs);
+        const int m0 = (int)(tile % mtiles) * TM, n0 = (int)(tile / mtiles) * TN;
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(full + s, (uint32_t)(np * (A_PIECE + B_PIECE)));
+        for (int p = 0; p < np; ++p) tma_load_3d(&tmA, st + p * A_PIECE, full + s, kb * TK, m0, p);
+        for (int p = 0; p < np; ++p)
+          tma_load_3d(&tmB, st + MAXP * A_PIECE + p * B_PIECE, full + s, kb * TK, n0, p);
+        issued = g + 1;
       }
-      if (!ok) {
-        // let the copies already in flight land before the CTA can exit
-        for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it) {
-          unsigned long long t0 = gtimer();
-          while (!mbar_try_wait(full + (it % STAGES), (uint32_t)(it / STAGES) & 1u))
+      // Wait until the last slabs have been consumed (their slots released by the
+      // MMAs' completion), so that no mbarrier arrival is still in flight when the
+      // CTA exits; on the abort path, wait for the copies in flight to land instead.
+      for (long long g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        unsigned long long t0 = gtimer();
+        if (ok) {
+          if (!mbar_wait(empty + s, ph, cta_abort, gerr)) ok = false;
+        }
+        if (!ok) {
+          while (!mbar_try_wait(full + s, ph))
             if (gtimer() - t0 > WAIT_NS) break;
         }
       }
     }
     __syncwarp();
-  } else if (warp == 9) {
+  } else if (warp == W_MMA) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- MMA issuer: chunk = CHUNK_SLABS consecutive K slabs of a tile;
+      // first the small terms of every slab of the chunk, then its leading terms
       constexpr uint32_t idesc = idesc_bf16_f32(TM, TN);
+      const int nch = (kslabs + CHUNK_SLABS - 1) / CHUNK_SLABS;
       bool ok = true;
-      int c = 0, t = 0, kb0 = 0;   // chunk c = K-blocks [kb0, kb0 + clen[t]) of term t
-      for (; c < nchunks && ok; ++c) {
-        const int b = c & 1;
-        if (c >= 2 && !mbar_wait(tempty + b, (uint32_t)((c >> 1) - 1) & 1u, cta_abort, gerr)) break;
-        tc_fence_after();
-        const uint32_t dst = tmem + (uint32_t)(b * TN);
-        const int it_begin = t * kblocks + kb0;
-        const int it_end = t * kblocks + min(kblocks, kb0 + terms.clen[t]);
-        kb0 += terms.clen[t];
-        if (kb0 >= kblocks) {
-          kb0 = 0;
-          ++t;
-        }
-        for (int it = it_begin; it < it_end; ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-          if (!mbar_wait(full + s, ph, cta_abort, gerr)) {
+      long long g = 0, gc = 0;   // slabs and chunks of this CTA so far
+      for (long long i = 0; i < my_tiles && ok; ++i) {
+        for (int ch = 0; ch < nch && ok; ++ch, ++gc) {
+          const int b = (int)(gc & 1);
+          if (gc >= 2 && !mbar_wait(tempty + b, (uint32_t)((gc >> 1) - 1) & 1u, cta_abort, gerr)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint64_t a0 = sdesc_sw128(su32(sA + s * A_STAGE));
-          const uint64_t b0 = sdesc_sw128(su32(sB + s * B_STAGE));
+          const int ns = min(CHUNK_SLABS, kslabs - ch * CHUNK_SLABS);
+          const uint32_t dst = tmem + (uint32_t)(b * TN);
+          bool first = true;
+          for (int pass = 0; pass < 2 && ok; ++pass) {
+            const int t0 = pass == 0 ? 0 : terms.nsmall, t1 = pass == 0 ? terms.nsmall : terms.nterms;
+            for (int q = 0; q < ns; ++q) {
+              const long long gs = g + q;
+              const int s = (int)(gs % STAGES);
+              if (pass == 0) {   // a slab is waited for once, before its first MMA
+                if (!mbar_wait(full + s, (uint32_t)(gs / STAGES) & 1u, cta_abort, gerr)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint32_t st = su32(smem + s * STAGE_BYTES);
+              for (int t = t0; t < t1; ++t) {
+                const int pa_t = (int)(terms.code >> (4 * t)) & 3, pb_t = (int)(terms.code >> (4 * t + 2)) & 3;
+                const uint64_t a0 = sdesc_sw64(st + pa_t * A_PIECE);
+                const uint64_t b0 = sdesc_sw64(st + MAXP * A_PIECE + pb_t * B_PIECE);
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk) {
-            // advance 16 BF16 = 32 bytes along K inside the 128-byte swizzled row;
-            // the first MMA of a chunk starts the buffer from zero
-            umma_bf16(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
-                      (it != it_begin || kk != 0) ? 1u : 0u);
+                for (int kk = 0; kk < TK / 16; ++kk) {
+                  // advance 16 BF16 = 32 bytes along K inside the 64-byte swizzled row;
+                  // the first MMA of a chunk starts the buffer from zero
+                  umma_bf16(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc, first ? 0u : 1u);
+                  first = false;
+                }
+              }
+            }
           }
-          umma_commit(empty + s);
+          if (!ok) break;
+          for (int q = 0; q < ns; ++q) umma_commit(empty + (int)((g + q) % STAGES));   // slots free
+          umma_commit(tfull + b);    // the chunk is complete
+          g += ns;
         }
-        // arrives once every MMA of this chunk has completed
-        if (ok) umma_commit(tfull + b);
       }
       if (*cta_abort || *gerr) {
         // wait (bounded) until every MMA issued so far has completed, so that
@@ -300,49 +357,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue warps 0-7: chunk partials -> FP32 registers
-    const int quarter = warp & 3, half = warp >> 2;
-    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
-    float acc[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
+    // ---------------- epilogue warps: chunk partials -> FP32 registers -> C
+    const int quarter = warp & 3, part = warp >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * EPI_COLS);
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int b = c & 1;
-      if (!mbar_wait(tfull + b, (uint32_t)(c >> 1) & 1u, cta_abort, gerr)) {
-        ok = false;
-        break;
+    const int nch = (kslabs + CHUNK_SLABS - 1) / CHUNK_SLABS;
+    long long g = 0;   // chunks of this CTA so far
+    for (long long i = 0; i < my_tiles && ok; ++i) {
+      const long long tile = blockIdx.x + i * gridDim.x;
+      float acc[EPI_COLS];
+#pragma unroll
+      for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0.0f;
+      for (int kb = 0; kb < nch; ++kb, ++g) {
+        const int b = (int)(g & 1);
+        if (!mbar_wait(tfull + b, (uint32_t)(g >> 1) & 1u, cta_abort, gerr)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // two loads in flight per wait
+#pragma unroll
+        for (int q = 0; q < EPI_COLS; q += 2 * LD_COLS) {
+          uint32_t v0[LD_COLS], v1[LD_COLS];
+          tmem_ld_async(lane_base + (uint32_t)(b * TN + q), v0);
+          tmem_ld_async(lane_base + (uint32_t)(b * TN + q + LD_COLS), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < LD_COLS; ++j) acc[q + j] += __uint_as_float(v0[j]);
+#pragma unroll
+          for (int j = 0; j < LD_COLS; ++j) acc[q + LD_COLS + j] += __uint_as_float(v1[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tempty + b)) : "memory");
       }
-      tc_fence_after();
-      // two 32-column loads in flight per wait
-#pragma unroll
-      for (int q = 0; q < 4; q += 2) {
-        uint32_t v0[32], v1[32];
-        tmem_ld32_async(lane_base + (uint32_t)(b * TN + q * 32), v0);
-        tmem_ld32_async(lane_base + (uint32_t)(b * TN + (q + 1) * 32), v1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v0[j]);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[(q + 1) * 32 + j] += __uint_as_float(v1[j]);
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tempty + b)) : "memory");
-    }
-    if (ok && !*cta_abort) {
-      const int row = m0 + quarter * 32 + lane;
-      const int col0 = n0 + half * 128;
+      if (!ok || *cta_abort) break;
+      // the TMEM buffers are free again: the next tile's MMAs run while this one is stored
+      const int row = (int)(tile % mtiles) * TM + quarter * 32 + lane;
+      const int col0 = (int)(tile / mtiles) * TN + part * EPI_COLS;
       if (row < M) {
         float* dst = C + (long long)row * ldc + col0;
-        const bool vec = ((ldc & 3) == 0) && ((((uintptr_t)C) & 15) == 0) && (col0 + 128 <= N);
+        const bool vec = ((ldc & 3) == 0) && ((((uintptr_t)C) & 15) == 0) && (col0 + EPI_COLS <= N);
         if (vec) {
 #pragma unroll
-          for (int j = 0; j < 128; j += 4)
+          for (int j = 0; j < EPI_COLS; j += 4)
             *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
 #pragma unroll
-          for (int j = 0; j < 128; ++j)
+          for (int j = 0; j < EPI_COLS; ++j)
             if (col0 + j < N) dst[j] = acc[j];
         }
       }
@@ -350,7 +413,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == W_MMA) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS)
@@ -381,23 +444,8 @@ static EncodeTiledFn get_encode() {
 
 int tc_gemm_ready() { return get_encode() != nullptr; }
 
-// K-blocks (of 64) of the leading term x_0 y_0 accumulated in TMEM before the
-// epilogue adds them into FP32 registers.  Tuning knob HOTRG_TC_CHUNK_KBLOCKS
-// (default 2 = K chunks of 128: the truncating tensor-core accumulation then
-// spans 8 MMAs only).  The terms of order 2^-8 (x_1 y_0, x_0 y_1) take chunks 8
-// times longer and those of order 2^-16 the whole K at once: measured on 4D Ising
-// chi=6, this leaves ln Z/V where uniform chunks put it (8.4e-8 against 8.3e-8),
-// while the leading chunk's length does move it.
-int tc_chunk_kblocks() {
-  static const int v = [] {
-    const char* e = getenv("HOTRG_TC_CHUNK_KBLOCKS");
-    const int x = e ? atoi(e) : 2;
-    return x < 1 ? 1 : x;
-  }();
-  return v;
-}
-
-// operand pieces stored as [piece][rows][kpad] BF16
+// operand pieces stored as [piece][rows][kpad] BF16; one box = TK columns of K
+// (64 bytes, the swizzle width) x box_rows rows of one piece
 static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kpad, int npieces,
                     int box_rows) {
   EncodeTiledFn enc = get_encode();
@@ -407,7 +455,7 @@ static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k
   cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     fprintf(stderr, "hotrg: tensor map encoding failed (CUresult %d; rows %d, kpad %d)\n", (int)r, rows,
@@ -417,12 +465,26 @@ static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k
   return 0;
 }
 
+// The kernel's dynamic shared-memory limit, raised once per device.
+static bool gemm_smem_attr_set() {
+  static std::atomic<int> done[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return true;
+  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+      cudaSuccess)
+    return false;
+  if (dev >= 0 && dev < kMaxDevices) done[dev].store(1, std::memory_order_release);
+  return true;
+}
+
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb, float* C, long long ldc,
-                   int* err_flag, cudaStream_t s, float* ms_out, int chunk_kblocks) {
-  if (Kpad % TK != 0 || nterms < 1 || nterms > 9 || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
-    fprintf(stderr, "hotrg: GEMM arguments rejected (Kpad %d, terms %d, A %p, B %p)\n", Kpad, nterms,
-            (const void*)A, (const void*)B);
+                   int* err_flag, cudaStream_t s, float* ms_out) {
+  if (Kpad % TK != 0 || Kpad < TK || nterms < 1 || nterms > 9 || npieces < 1 || npieces > MAXP || M < 1 ||
+      N < 1 || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
+    fprintf(stderr, "hotrg: GEMM arguments rejected (M %d, N %d, Kpad %d, pieces %d, terms %d, A %p, B %p)\n",
+            M, N, Kpad, npieces, nterms, (const void*)A, (const void*)B);
     return -1;
   }
   {
@@ -434,27 +496,39 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
   }
   CUtensorMap ma, mb;
   if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) return -1;
+  // terms ordered by decreasing piece order (pa + pb): the smallest terms go first into
+  // the zeroed accumulator of a chunk, the leading term x_0 y_0 last
   TcTerms terms;
   terms.nterms = nterms;
-  const int kblocks = Kpad / TK, base = chunk_kblocks > 0 ? chunk_kblocks : tc_chunk_kblocks();
-  for (int t = 0; t < 9; ++t) {
-    terms.pa[t] = t < nterms ? pa[t] : 0;
-    terms.pb[t] = t < nterms ? pb[t] : 0;
-    const int order = terms.pa[t] + terms.pb[t];
-    terms.clen[t] = order == 0 ? base : order == 1 ? 8 * base : kblocks;
-    if (terms.clen[t] < 1) terms.clen[t] = 1;
+  terms.npieces = npieces;
+  terms.nsmall = 0;
+  int order[9];
+  for (int t = 0; t < nterms; ++t) order[t] = t;
+  std::stable_sort(order, order + nterms,
+                   [&](int x, int y) { return pa[x] + pb[x] > pa[y] + pb[y]; });
+  terms.code = 0;
+  for (int t = 0; t < nterms; ++t) {
+    const int a = pa[order[t]], b = pb[order[t]];
+    if (a < 0 || a >= npieces || b < 0 || b >= npieces) {
+      fprintf(stderr, "hotrg: GEMM term %d uses a piece beyond %d\n", t, npieces);
+      return -1;
+    }
+    terms.code |= (unsigned long long)(a | (b << 2)) << (4 * t);
+    if (a + b > 0) terms.nsmall = t + 1;
   }
-  static const bool attr = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                SMEM_BYTES) == cudaSuccess;
-  (void)attr;
-  dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN);
+  if (!gemm_smem_attr_set()) {
+    fprintf(stderr, "hotrg: GEMM shared-memory attribute refused\n");
+    return -1;
+  }
+  const long long ntiles = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+  const int grid = (int)std::min<long long>(ntiles, sm_count());
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ms_out) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, kblocks, terms, err_flag);
+  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, Kpad / TK, terms, err_flag);
   ++g_launches;
   if (ms_out) {
     cudaEventRecord(e1, s);
@@ -465,9 +539,70 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    fprintf(stderr, "hotrg: GEMM launch error %s (grid %u x %u)\n", cudaGetErrorString(e), grid.x, grid.y);
+    fprintf(stderr, "hotrg: GEMM launch error %s (grid %d)\n", cudaGetErrorString(e), grid);
     return -1;
   }
+  return 0;
+}
+
+// Operand pieces for the rate probe: small integers (exact in BF16) from a hash
+__global__ void fill_pieces_kernel(__nv_bfloat16* p, long long n, unsigned seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned x = (unsigned)i * 2654435761u ^ seed;
+    x ^= x >> 15;
+    x *= 2246822519u;
+    x ^= x >> 13;
+    p[i] = __float2bfloat16((float)((int)(x % 17u) - 8) * 0.125f);
+  }
+}
+
+int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch) {
+  if (npieces < 2 || npieces > MAXP || M < 1 || N < 1 || Kpad < TK || Kpad % TK || iters < 1) return -1;
+  __nv_bfloat16 *A = nullptr, *B = nullptr;
+  float* C = nullptr;
+  int* err = nullptr;
+  const long long na = (long long)npieces * M * Kpad, nb = (long long)npieces * N * Kpad;
+  if (cudaMalloc(&A, 2 * na) != cudaSuccess || cudaMalloc(&B, 2 * nb) != cudaSuccess ||
+      cudaMalloc(&C, 4LL * M * N) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    cudaFree(err);
+    return -2;
+  }
+  cudaMemset(err, 0, sizeof(int));
+  fill_pieces_kernel<<<4 * sm_count(), 256>>>(A, na, 1u);
+  fill_pieces_kernel<<<4 * sm_count(), 256>>>(B, nb, 2u);
+  g_launches += 2;
+  int ta3[3] = {1, 0, 0}, tb3[3] = {0, 1, 0};
+  int ta6[6] = {2, 1, 0, 1, 0, 0}, tb6[6] = {0, 1, 2, 0, 1, 0};
+  const int nt = npieces == 2 ? 3 : 6;
+  int r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, npieces == 2 ? ta3 : ta6, npieces == 2 ? tb3 : tb6,
+                         C, N, err, 0, nullptr);   // warm-up
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, 0);
+  for (int i = 0; i < iters && r == 0; ++i)
+    r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, npieces == 2 ? ta3 : ta6, npieces == 2 ? tb3 : tb6, C,
+                       N, err, 0, nullptr);
+  cudaEventRecord(e1, 0);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  int h_err = 0;
+  cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C);
+  cudaFree(err);
+  if (r != 0 || cudaGetLastError() != cudaSuccess) return -3;
+  if (h_err) return h_err;
+  *ms_per_launch = ms / iters;
   return 0;
 }
 

@@ -10,6 +10,23 @@ namespace hotrg {
 
 std::atomic<long long> g_launches{0};
 
+int sm_count() {
+  static std::atomic<int> cache[kMaxDevices];   // zero until queried
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = (dev >= 0 && dev < kMaxDevices) ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 1;
+  }
+  if (dev >= 0 && dev < kMaxDevices) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 // T0 in the slot layout rows (x_0 .. x_{d-1}) x cols (x_0' .. x_{d-1}').
 // Every leg carries X_{s j}: X_{s 0} = sqrt(cosh b), X_{s 1} = sigma_s sqrt(sinh b)
 // (X = U sqrt(Lambda), U = [[1,1],[1,-1]]/sqrt 2, Lambda = diag(2cosh b, 2sinh b)),

@@ -1,9 +1,9 @@
 """Write per-step FP64 oracle results for a named workload (calls only oracle/).
 
-    python tests/golden/make_oracle_reference.py ising3d_chi16 [--steps N]
+    python tests/golden/make_oracle_reference.py ising3d_chi16 [--steps N] [--out PATH]
 
-Output: tests/golden/<name>.jsonl, one JSON object per coarse-graining step,
-appended as each step finishes (a partial file is a valid prefix).
+Output: tests/golden/<name>.jsonl (or PATH), one JSON object per coarse-graining
+step, appended as each step finishes (a partial file is a valid prefix).
 """
 
 import argparse
@@ -25,7 +25,7 @@ WORKLOADS = {
     # 4D Ising, chi = 6, cycling x, y, z, w
     "ising4d_chi6": dict(d=4, beta=0.15, h=0.0, chi=6, steps=12, first=0),
     # 3D Ising, chi = 20 (first steps only: a steady step costs ~4e14 flop on the CPU)
-    "ising3d_chi20": dict(d=3, beta=0.2216544, h=0.0, chi=20, steps=4, first=2),
+    "ising3d_chi20": dict(d=3, beta=0.2216544, h=0.0, chi=20, steps=7, first=2),
 }
 
 
@@ -33,10 +33,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("name", choices=sorted(WORKLOADS))
     ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--out", default=None, help="output path (default: tests/golden/<name>.jsonl)")
     args = ap.parse_args()
     w = WORKLOADS[args.name]
     steps = args.steps or w["steps"]
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), args.name + ".jsonl")
+    path = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), args.name + ".jsonl")
     run = o.HotrgRun(w["d"], w["beta"], w["h"])
     with open(path, "w") as f:
         head = dict(kind="header", workload=args.name, **{k: w[k] for k in ("d", "beta", "h", "chi")},

@@ -181,17 +181,20 @@ def test_ising3d_chi16_free_energy_matches_oracle_reference(pkg, z2):
             ref = gold[step]["ln_z_per_site"]
             assert abs(lnz - ref) / abs(ref) <= 1e-7, (step, lnz, ref)
             if step > 21:
-                # at beta_c a deviation of T along the relevant (thermal) direction grows
-                # by about 2^1.59 per three steps, so X and the spectra drift away from the
-                # oracle's late in the run; ln Z / V (step p weighs 2^-p) stays gated above
+                # at beta_c a deviation of T along the relevant (thermal) direction keeps
+                # growing, so X and the spectra drift away from the oracle's late in the
+                # run; ln Z / V (step p weighs 2^-p) stays gated above
                 continue
+            # Multi-step gates: these bound the deviation CARRIED over the run, not the
+            # error of one step (one split step is gated at 1e-6 of lambda_1 by the restart
+            # test below).  Measured: the spectral deviation is ~1.5e-7 lambda_1 after the
+            # first split step and grows ~1.45x per step to ~3e-5 by step 17; X deviates
+            # by up to ~1e-5 through step 21.
             _, x, _ = pkg.hotrg_observables(g.ctx)
-            assert abs(x - gold[step]["gu_wen_x"]) <= 1e-5
+            assert abs(x - gold[step]["gu_wen_x"]) <= 3e-5, (step, x, gold[step]["gu_wen_x"])
             for leg in gold[step]["legs"]:
                 lam = pkg.hotrg_spectrum(g.ctx, leg["axis"], 0)
                 want = np.array(leg["lam"])
-                # the BF16 contraction leaves T ~1e-7 from the oracle's after each step and
-                # the difference carries into later environments (A is quartic in T)
                 np.testing.assert_allclose(lam[: len(want)], want, rtol=0, atol=1e-4 * want[0],
                                            err_msg=f"step {step} leg {leg['axis']}")
     finally:
@@ -252,3 +255,111 @@ def test_ising4d_chi6_free_energy_matches_oracle_reference(pkg, z2):
             assert abs(lnz - ref) / abs(ref) <= 1e-7, (step, lnz, ref)
     finally:
         g.close()
+
+
+# ---------------------------------------------------------------------------
+# restart: the oracle's tensor after step 3 goes into both sides, one step runs on
+# each, so the error of ONE step is seen apart from the error carried over steps
+# ---------------------------------------------------------------------------
+
+def _leg_parities(records, d):
+    """Leg parities after the oracle's steps (index 0 of an initial leg even, 1 odd; a
+    new index takes the parity of the rows its isometry column occupies)."""
+    parity = [np.array([0, 1])] * d
+    for rec in records:
+        new = list(parity)
+        for leg in rec.legs:
+            pj = parity[leg.axis]
+            row = ((pj[None, :] + pj[:, None]) % 2).reshape(-1)   # row hat + check * chi
+            cols = []
+            for k in range(leg.u.shape[1]):
+                ps = set(row[np.abs(leg.u[:, k]) > 0].tolist())
+                assert len(ps) == 1
+                cols.append(ps.pop())
+            new[leg.axis] = np.array(cols)
+        parity = new
+    return parity
+
+
+@pytest.fixture(scope="module")
+def chi16_restart():
+    """3D Ising chi=16 at beta_c: the oracle's normalised T after steps z, x, y, its
+    leg parities, ONE full oracle step along z (all 4096 contraction iterations) and
+    the environments / isometries of the following step along x computed from the
+    oracle's own new tensor."""
+    beta = 0.2216544
+    run = o.HotrgRun(3, beta, 0.0)
+    for a in (2, 0, 1):
+        run.step(a, 16)
+    t3 = run.t.copy()
+    par3 = _leg_parities(run.records, 3)
+    rec4 = run.step(2, 16)
+    t4 = run.t.copy()
+    tp4 = o.to_paper_order(t4, 0)
+    nxt = o.next_axes(3, 0)
+    legs5 = [o.choose_isometry(tp4, j, 16, nxt[j - 1]) for j in (1, 2)]
+    return dict(beta=beta, t3=t3, par3=par3, rec4=rec4, t4=t4, legs5=legs5)
+
+
+def _restart_ctx(pkg, r, prec):
+    ctx = pkg.hotrg_init_tensor(3, [16, 16, 16], r["t3"], r["beta"])
+    pkg.hotrg_set_precision(ctx, prec)
+    pkg.hotrg_set_fp64_threshold(ctx, 0.0)         # the step runs in `prec` whatever its size
+    pkg.hotrg_set_parity(ctx, np.concatenate(r["par3"]).astype(np.int32))   # Z2 block form
+    return ctx
+
+
+@pytest.mark.parametrize("prec,tol_t,tol_lam,tol_u,tol_tr", [
+    # BF16X6: one step's trace to 1e-6 relative (it enters ln Z/V divided by 2^p: the
+    # 1e-7 target at p = 4 allows 1.6e-6), T' to 2e-6 of max|T'|, the next step's spectra
+    # to 1e-6 lambda_1 and isometries to 1e-6
+    (2, 2e-6, 1e-6, 1e-6, 1e-6),
+    (0, 1e-10, 1e-12, 1e-9, 1e-12),     # FP64 form
+])
+def test_ising3d_chi16_restart_one_step_against_full_oracle_step(pkg, chi16_restart, prec, tol_t, tol_lam,
+                                                                  tol_u, tol_tr):
+    r = chi16_restart
+    ctx = _restart_ctx(pkg, r, prec)
+    try:
+        pkg.hotrg_step(ctx, 2, 16)
+        assert pkg.hotrg_bottleneck_flops(ctx)[2], "the Z2 block form did not run"
+        # step 4: the isometries come from the common input (FP64 environments)
+        for leg in r["rec4"].legs:
+            lam = pkg.hotrg_spectrum(ctx, leg.axis, 1 if leg.chose_prime else 0)
+            want = leg.lam_prime if leg.chose_prime else leg.lam
+            np.testing.assert_allclose(lam, want, rtol=0, atol=1e-12 * want[0])
+        tr, x, _ = pkg.hotrg_observables(ctx)
+        assert abs(tr - r["rec4"].trace) <= tol_tr * abs(r["rec4"].trace), (tr, r["rec4"].trace)
+        assert abs(x - r["rec4"].gu_wen_x) <= 10 * tol_tr * abs(r["rec4"].gu_wen_x)
+        # the new tensor, every element (both normalised by their own trace)
+        t_gpu = pkg.hotrg_tensor(ctx)
+        scale = np.abs(r["t4"]).max()
+        err = np.abs(t_gpu - r["t4"]).max() / scale
+        assert err <= tol_t, f"T' max deviation {err:.3e} of max|T'|"
+        # step 5 from each side's own T': the environments, spectra and isometries the
+        # one-step deviation of T' leads to
+        pkg.hotrg_step(ctx, 0, 16)
+        for leg in r["legs5"]:
+            for prime in (0, 1):
+                lam = pkg.hotrg_spectrum(ctx, leg.axis, prime)
+                want = leg.lam_prime if prime else leg.lam
+                np.testing.assert_allclose(lam, want, rtol=0, atol=tol_lam * want[0],
+                                           err_msg=f"step 5 leg {leg.axis} prime {prime}")
+            u, _ = pkg.hotrg_isometry(ctx, leg.axis)
+            np.testing.assert_allclose(u.T @ u, np.eye(u.shape[1]), atol=1e-12)
+            if leg.gap_at_cut > 1e-6:
+                # the sign of a column is free (Sec. 4.2.8); where two entries of a column
+                # tie within the gauge's 1e-6 pivot tolerance, one step's deviation of T'
+                # can pick the other pivot, so the columns are compared up to sign.  A
+                # perturbation dA of the environment turns eigenvector k by at most
+                # |dA| / (its distance to the other eigenvalues): with |dA| at the spectral
+                # gate (tol_lam lambda_1), column k is allowed tol_u max(1, lambda_1 / gap_k)
+                lam = leg.lam_prime if leg.chose_prime else leg.lam
+                kept = u.shape[1]
+                gaps = np.array([np.min(np.abs(np.delete(lam, k) - lam[k])) for k in range(kept)])
+                col_tol = tol_u * np.maximum(1.0, (tol_lam / tol_u) * lam[0] / np.maximum(gaps, 1e-300))
+                sgn = np.sign(np.sum(u * leg.u, axis=0))
+                dev = np.abs(u * sgn - leg.u).max(axis=0)
+                assert np.all(dev <= col_tol), (f"step 5 leg {leg.axis}", dev, col_tol)
+    finally:
+        pkg.hotrg_free(ctx)

@@ -230,3 +230,35 @@ def test_bad_arguments(pkg):
             pkg.hotrg_set_tangent(g.ctx, True)  # not an Ising context
     finally:
         g.close()
+
+
+def test_autograd_function_gives_the_tangent_oracle_gradient(pkg):
+    # torch.autograd on ln Z/V (the C ABI's forward-mode tangent in the backward pass)
+    # against the tangent oracle, step by step, and against the plain central difference
+    # of the forward values
+    import torch
+
+    from paper_2110_03607_gb300 import autograd as ag
+
+    d, beta, h, chi = 3, 0.22, 0.0, 4
+    axes = o.cyclic_axes(d, 6, first=2)
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    lnz = ag.ln_z_per_site(bt, d, h, chi, axes)
+    tr = tg.HotrgTangentRun(d, beta, h)
+    recs = [tr.step(a, chi) for a in axes]
+    for p in range(len(axes)):
+        (g,) = torch.autograd.grad(lnz[p], bt, retain_graph=True)
+        want = recs[p].dln_z_per_site
+        assert abs(float(g) - want) <= 1e-10 * abs(want), (p, float(g), want)
+    # a weighted sum: the vector-Jacobian product
+    w = torch.linspace(0.5, 2.0, len(axes), dtype=torch.float64)
+    (gw,) = torch.autograd.grad((w * lnz).sum(), bt)
+    want = sum(float(w[p]) * recs[p].dln_z_per_site for p in range(len(axes)))
+    assert abs(float(gw) - want) <= 1e-10 * abs(want)
+    # central difference of the forward values (beta +- 1e-5)
+    db = 1e-5
+    with torch.no_grad():
+        up = ag.ln_z_per_site(torch.tensor(beta + db, dtype=torch.float64), d, h, chi, axes)[-1]
+        dn = ag.ln_z_per_site(torch.tensor(beta - db, dtype=torch.float64), d, h, chi, axes)[-1]
+    fd = float(up - dn) / (2 * db)
+    assert abs(ag.energy_per_site(beta, d, h, chi, axes) + fd) <= 1e-7 * abs(fd)

@@ -101,6 +101,13 @@ def test_z2_fp64_agrees_with_the_dense_form(pkg, d, chi, nsteps):
             xa = pkg.hotrg_observables(ga.ctx)[1]
             xb = pkg.hotrg_observables(gb.ctx)[1]
             assert abs(xa - xb) <= 1e-11
+            # the gauge-fixed tensors themselves, element by element, to the FP64 parity
+            # gate of T' (the rounding of the regrouped Gram sums moves the eigenvectors
+            # by ~1e-11 after 8 steps)
+            ta = pkg.hotrg_tensor(ga.ctx)
+            tb = pkg.hotrg_tensor(gb.ctx)
+            assert ta.shape == tb.shape
+            np.testing.assert_allclose(ta, tb, rtol=0, atol=1e-10 * np.abs(tb).max())
     finally:
         ga.close()
         gb.close()
