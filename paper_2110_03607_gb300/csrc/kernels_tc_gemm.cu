@@ -4,23 +4,31 @@
 // with both operands split into BF16 pieces, x = x_0 + x_1 (+ x_2), and the
 // product formed as a sum of piece products (terms) x_i y_j.
 //
-// Persistent kernel: one CTA per SM walks the 128 x 256 tiles of C (tile index
-// blockIdx.x, + gridDim.x, ...; row tiles fastest, so the CTAs running at one time
-// share the B tiles in L2).  Warp 8 (one lane) streams 32-wide K slabs into a
-// 3-stage shared-memory ring with TMA (64-byte swizzle); one stage holds EVERY
-// piece of the A and B slabs (3 x 8 KiB + 3 x 16 KiB), so each piece is loaded
-// once per slab and serves all the terms that use it.  Warp 9 (one lane) issues
-// tcgen05.mma (M=128, N=256, K=16, kind::f16, BF16 x BF16 -> FP32).  The tensor
-// core's FP32 accumulation truncates, so a long accumulation drifts towards zero:
-// the K range is therefore cut into chunks of CHUNK_SLABS slabs, each accumulated
-// from zero in one of two TMEM buffers (256 columns each, used alternately) while
-// warps 0-7 drain the other buffer with tcgen05.ld (warp w owns TMEM lanes
-// 32(w%4).. and columns 128(w/4)..) and add the chunk into FP32 registers with
-// round-to-nearest.  Within a chunk the small terms (order 2^-16, then 2^-8) of
-// all its slabs go first, the leading term x_0 y_0 last: the small terms then
-// truncate at their own (small) scale and only the leading MMAs truncate at the
-// scale of the result.  Every mbarrier wait is bounded in time; an expired wait
-// sets a global error flag that also makes the other CTAs give up.
+// Two persistent kernels; launch_tc_gemm uses the CTA-pair one (HOTRG_TC_USE_PAIR).
+//
+// tc_gemm_pair_kernel (cta_group::2): a cluster of two CTAs on two SMs computes a
+// 256 x 256 tile of C; CTA 0 issues tcgen05.mma with M = 256, N = 256, K = 16.  CTA r
+// holds rows 128 r .. of the A tile and rows 128 r .. of the B tile, so each SM
+// receives only half of the B tile: the per-SM copy rate, not the tensor pipe or the
+// L2, is what bounds the one-CTA form below.  K slabs of 64 BF16 (128-byte rows,
+// 128-byte swizzle), every piece of a slab in one of two 96 KiB ring stages.
+//
+// tc_gemm_kernel (cta_group::1): one CTA per SM walks 128 x 256 tiles; K slabs of 32
+// BF16 (64-byte rows) in a 3-stage ring, every piece of a slab in one stage.
+//
+// In both, the CTAs walk the tiles (tile index blockIdx.x, + gridDim.x, ...; row
+// tiles fastest, so the CTAs running at one time share the B tiles in L2); one lane of
+// one warp streams the slabs with TMA, one lane of another issues the MMAs (BF16 x
+// BF16 -> FP32) and releases ring slots with tcgen05.commit.  The tensor core's FP32
+// accumulation truncates, so a long accumulation drifts towards zero: the K range is
+// therefore cut into chunks of 64, each accumulated from zero in one of two TMEM
+// buffers (used alternately) while eight epilogue warps drain the other buffer with
+// tcgen05.ld (warp w owns TMEM lanes 32(w%4)..) and add the chunk into FP32 registers
+// with round-to-nearest.  Within a chunk the small terms (order 2^-16, then 2^-8) go
+// first, the leading term x_0 y_0 last: the small terms then truncate at their own
+// (small) scale and only the four leading MMAs truncate at the scale of the result.
+// Every mbarrier wait is bounded in time; an expired wait sets a global error flag
+// that also makes the other CTAs give up.
 #include <cuda.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -34,11 +42,26 @@
 namespace hotrg {
 
 namespace {
-constexpr int TM = 128, TN = 256, TK = 32, STAGES = 3, MAXP = 3;
-constexpr int A_PIECE = TM * TK * 2;                      // 8 KiB
-constexpr int B_PIECE = TN * TK * 2;                      // 16 KiB
-constexpr int STAGE_BYTES = MAXP * (A_PIECE + B_PIECE);   // 72 KiB
-constexpr int TMEM_COLS = 512;         // two 256-column FP32 accumulators
+// Tile TM x TN of C per CTA; K slabs of TK BF16 (TK = 64: 128-byte rows with the
+// 128-byte swizzle; TK = 32: 64-byte rows with the 64-byte swizzle); a ring of STAGES
+// stages, each holding every piece of one slab of A and B.
+#ifndef HOTRG_TC_TN
+#define HOTRG_TC_TN 256
+#endif
+#ifndef HOTRG_TC_TK
+#define HOTRG_TC_TK 32
+#endif
+#ifndef HOTRG_TC_STAGES
+#define HOTRG_TC_STAGES 3
+#endif
+constexpr int TM = 128, TN = HOTRG_TC_TN, TK = HOTRG_TC_TK, STAGES = HOTRG_TC_STAGES, MAXP = 3;
+static_assert(TK == 32 || TK == 64, "K slab of 32 or 64 BF16");
+static_assert(TN == 128 || TN == 256, "N tile of 128 or 256");
+constexpr int A_PIECE = TM * TK * 2;
+constexpr int B_PIECE = TN * TK * 2;
+constexpr int STAGE_BYTES = MAXP * (A_PIECE + B_PIECE);
+constexpr int TMEM_COLS = 2 * TN;      // two TN-column FP32 accumulators
+constexpr int SW_BYTES = TK * 2;       // swizzle width = row length in bytes
 // Epilogue warps: EPI_WARPS / 4 per TMEM lane quarter, each draining EPI_COLS columns
 #ifndef HOTRG_TC_EPI_WARPS
 #define HOTRG_TC_EPI_WARPS 8
@@ -50,12 +73,13 @@ constexpr int LD_COLS = EPI_WARPS == 8 ? 32 : 16;   // columns per tcgen05.ld
 constexpr int W_PROD = EPI_WARPS, W_MMA = EPI_WARPS + 1;
 constexpr int NTHREADS = 32 * (EPI_WARPS + 2);      // epilogue warps + producer + MMA
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
 }  // namespace
 
-// K slabs per accumulation chunk (chunk length 32 x this along K)
+// K slabs per accumulation chunk (chunk length TK x this along K; 64 by default)
 #ifndef HOTRG_TC_CHUNK_SLABS
-#define HOTRG_TC_CHUNK_SLABS 2
+#define HOTRG_TC_CHUNK_SLABS (64 / HOTRG_TC_TK)
 #endif
 constexpr int CHUNK_SLABS = HOTRG_TC_CHUNK_SLABS;
 static_assert(CHUNK_SLABS >= 1 && CHUNK_SLABS < STAGES, "a chunk must leave a ring stage to prefetch into");
@@ -131,16 +155,16 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, void* dst, u
       : "memory");
 }
 
-// Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with the 64-byte swizzle: rows of 64 bytes (32 BF16 along K), 8-row groups
-// 512 bytes apart (the swizzle pattern repeats every 512 bytes).
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA with
+// the SW_BYTES swizzle: rows of SW_BYTES bytes (TK BF16 along K), 8-row groups
+// 8 SW_BYTES apart (the swizzle pattern repeats every 8 rows).
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
-  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for this layout)
+  d |= (uint64_t)((8 * SW_BYTES) >> 4) << 32;       // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)(SW_BYTES == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
   return d;
 }
 
@@ -328,11 +352,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const uint32_t st = su32(smem + s * STAGE_BYTES);
               for (int t = t0; t < t1; ++t) {
                 const int pa_t = (int)(terms.code >> (4 * t)) & 3, pb_t = (int)(terms.code >> (4 * t + 2)) & 3;
-                const uint64_t a0 = sdesc_sw64(st + pa_t * A_PIECE);
-                const uint64_t b0 = sdesc_sw64(st + MAXP * A_PIECE + pb_t * B_PIECE);
+                const uint64_t a0 = sdesc_sw(st + pa_t * A_PIECE);
+                const uint64_t b0 = sdesc_sw(st + MAXP * A_PIECE + pb_t * B_PIECE);
 #pragma unroll
                 for (int kk = 0; kk < TK / 16; ++kk) {
-                  // advance 16 BF16 = 32 bytes along K inside the 64-byte swizzled row;
+                  // advance 16 BF16 = 32 bytes along K inside the swizzled row;
                   // the first MMA of a chunk starts the buffer from zero
                   umma_bf16(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc, first ? 0u : 1u);
                   first = false;
@@ -422,6 +446,273 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// CTA-pair form (cta_group::2): a cluster of two CTAs on two SMs computes a 256 x 256
+// tile of C with M = 256 MMAs issued by CTA 0.  CTA r holds rows 128 r .. of the A
+// tile and rows 128 r .. of the B tile (N) in its own shared memory, so each SM
+// receives half of B; K slabs of 64 BF16 (128-byte rows, 128-byte swizzle), every
+// piece of a slab in one of two ring stages (96 KiB each).  CTA r's TMEM holds rows
+// 128 r .. of the accumulator.  CTA 1's copies complete on its own barrier; a thread
+// of CTA 1 then arrives on CTA 0's barrier, whose MMA thread waits for both.  The
+// MMA completions arrive on the ring and accumulator barriers of both CTAs.
+// ---------------------------------------------------------------------------
+#ifndef HOTRG_TC_USE_PAIR
+#define HOTRG_TC_USE_PAIR 1
+#endif
+namespace {
+constexpr int P_TK = 64, P_STAGES = 2;
+constexpr int P_A_PIECE = 128 * P_TK * 2;                    // 16 KiB: this CTA's A rows
+constexpr int P_B_PIECE = 128 * P_TK * 2;                    // 16 KiB: this CTA's B rows
+constexpr int P_STAGE = MAXP * (P_A_PIECE + P_B_PIECE);      // 96 KiB
+constexpr int P_SMEM = 1024 + P_STAGES * P_STAGE + 256;
+constexpr int P_NTHREADS = 320;                              // 8 epilogue warps + producer + MMA/relay
+static_assert(P_SMEM <= 227 * 1024, "shared memory of one CTA");
+}  // namespace
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// arrival on the mbarrier at bar's offset in CTA `rank` of the cluster
+__device__ __forceinline__ void mbar_arrive_rank(uint64_t* bar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(bar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrives on the mbarrier at bar's offset in every CTA of cta_mask once the pair MMAs
+// issued so far by this thread have completed
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          su32(bar)),
+      "h"(cta_mask)
+      : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        float* __restrict__ C, int M, int N, long long ldc, int kslabs, TcTerms terms,
+                        int* g_err) {
+  extern __shared__ uint8_t smem_raw[];
+  volatile int* gerr = g_err;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + P_STAGES * P_STAGE);
+  uint64_t* empty = full + P_STAGES;
+  uint64_t* tfull = empty + P_STAGES;    // [2] MMA -> epilogue (both CTAs)
+  uint64_t* tempty = tfull + 2;          // [2] epilogue of both CTAs -> MMA (CTA 0)
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* cta_abort = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const bool leader = rank == 0;
+  const int mgroups = (M + 255) / 256;
+  const long long ngroups = (long long)mgroups * ((N + 255) / 256);
+  const long long cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const long long tiles_here = ngroups > cid ? (ngroups - 1 - cid) / ncl + 1 : 0;
+  auto grp = [&](long long i) { return cid + i * ncl; };
+  const int np = terms.npieces;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(full + s, leader ? 2 : 1);   // CTA 0: its own copies and CTA 1's relay
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, 16);             // the 8 epilogue warps of each CTA
+    }
+    mbar_init(drain, 1);
+    *cta_abort = *gerr ? 1 : 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
+  }
+  if (warp == 9) {
+    // one warp of each CTA of the pair allocates, collectively, the TMEM of both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // both CTAs' barriers and TMEM exist before any copy or arrival
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long my_tiles = *cta_abort ? 0 : tiles_here;
+  const long long total = my_tiles * kslabs;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs): this CTA's A rows and B rows
+      long long issued = 0;
+      bool ok = true;
+      for (long long g = 0; g < total; ++g) {
+        const int s = (int)(g % P_STAGES);
+        const uint32_t ph = (uint32_t)(g / P_STAGES) & 1u;
+        if (!mbar_wait(empty + s, ph ^ 1u, cta_abort, gerr)) {
+          ok = false;
+          break;
+        }
+        const long long gg = grp(g / kslabs);
+        const int kb = (int)(g % kslabs);
+        const int m0 = (int)(gg % mgroups) * 256 + (int)rank * 128;
+        const int nb0 = (int)(gg / mgroups) * 256 + (int)rank * 128;
+        uint8_t* st = smem + s * P_STAGE;
+        mbar_expect_tx(full + s, (uint32_t)(np * (P_A_PIECE + P_B_PIECE)));
+        for (int p = 0; p < np; ++p) tma_load_3d(&tmA, st + p * P_A_PIECE, full + s, kb * P_TK, m0, p);
+        for (int p = 0; p < np; ++p)
+          tma_load_3d(&tmB, st + MAXP * P_A_PIECE + p * P_B_PIECE, full + s, kb * P_TK, nb0, p);
+        issued = g + 1;
+      }
+      for (long long g = issued > P_STAGES ? issued - P_STAGES : 0; g < issued; ++g) {
+        const int s = (int)(g % P_STAGES);
+        const uint32_t ph = (uint32_t)(g / P_STAGES) & 1u;
+        unsigned long long t0 = gtimer();
+        if (ok && !mbar_wait(empty + s, ph, cta_abort, gerr)) ok = false;
+        if (!ok)
+          while (!mbar_try_wait(full + s, ph))
+            if (gtimer() - t0 > WAIT_NS) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 9) {
+    if (lane == 0 && !leader) {
+      // ---------------- relay (CTA 1): each slab of this CTA has landed -> CTA 0
+      for (long long g = 0; g < total; ++g) {
+        const int s = (int)(g % P_STAGES);
+        if (!mbar_wait(full + s, (uint32_t)(g / P_STAGES) & 1u, cta_abort, gerr)) break;
+        mbar_arrive_rank(full + s, 0);
+      }
+    } else if (lane == 0) {
+      // ---------------- MMA issuer (CTA 0): M = 256, N = 256, K = 16; one chunk per slab,
+      // its small terms first
+      constexpr uint32_t idesc = idesc_bf16_f32(256, 256);
+      bool ok = true;
+      for (long long g = 0; g < total && ok; ++g) {
+        const int b = (int)(g & 1);
+        if (g >= 2 && !mbar_wait(tempty + b, (uint32_t)((g >> 1) - 1) & 1u, cta_abort, gerr)) break;
+        tc_fence_after();
+        const int s = (int)(g % P_STAGES);
+        if (!mbar_wait(full + s, (uint32_t)(g / P_STAGES) & 1u, cta_abort, gerr)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dst = tmem + (uint32_t)(b * 256);
+        const uint32_t st = su32(smem + s * P_STAGE);
+        for (int t = 0; t < terms.nterms; ++t) {
+          const int pa_t = (int)(terms.code >> (4 * t)) & 3, pb_t = (int)(terms.code >> (4 * t + 2)) & 3;
+          const uint64_t a0 = sdesc_sw128(st + pa_t * P_A_PIECE);
+          const uint64_t b0 = sdesc_sw128(st + MAXP * P_A_PIECE + pb_t * P_B_PIECE);
+#pragma unroll
+          for (int kk = 0; kk < P_TK / 16; ++kk)
+            umma_bf16_pair(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
+                           (t != 0 || kk != 0) ? 1u : 0u);
+        }
+        umma_commit_pair(empty + s, (uint16_t)0x3);   // the slot of both CTAs is free
+        umma_commit_pair(tfull + b, (uint16_t)0x3);   // the chunk is in both CTAs' TMEM
+      }
+      if (*cta_abort || *gerr) {
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(drain))
+                     : "memory");
+        unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(drain, 0))
+          if (gtimer() - t0 > WAIT_NS) break;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue warps (both CTAs): this CTA's 128 rows of the tile
+    const int quarter = warp & 3, part = warp >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 128);
+    bool ok = true;
+    long long g = 0;
+    for (long long i = 0; i < my_tiles && ok; ++i) {
+      float acc[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
+      for (int kb = 0; kb < kslabs; ++kb, ++g) {
+        const int b = (int)(g & 1);
+        if (!mbar_wait(tfull + b, (uint32_t)(g >> 1) & 1u, cta_abort, gerr)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int q = 0; q < 128; q += 64) {
+          uint32_t v0[32], v1[32];
+          tmem_ld_async(lane_base + (uint32_t)(b * 256 + q), v0);
+          tmem_ld_async(lane_base + (uint32_t)(b * 256 + q + 32), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[q + j] += __uint_as_float(v0[j]);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[q + 32 + j] += __uint_as_float(v1[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_rank(tempty + b, 0);
+      }
+      if (!ok || *cta_abort) break;
+      const long long gg = grp(i);
+      const int row = (int)(gg % mgroups) * 256 + (int)rank * 128 + quarter * 32 + lane;
+      const int col0 = (int)(gg / mgroups) * 256 + part * 128;
+      if (row < M) {
+        float* dst = C + (long long)row * ldc + col0;
+        const bool vec = ((ldc & 3) == 0) && ((((uintptr_t)C) & 15) == 0) && (col0 + 128 <= N);
+        if (vec) {
+#pragma unroll
+          for (int j = 0; j < 128; j += 4)
+            *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 128; ++j)
+            if (col0 + j < N) dst[j] = acc[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // no CTA leaves while its peer may still use its TMEM or barriers
+  if (warp == 9) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -445,17 +736,17 @@ static EncodeTiledFn get_encode() {
 int tc_gemm_ready() { return get_encode() != nullptr; }
 
 // operand pieces stored as [piece][rows][kpad] BF16; one box = TK columns of K
-// (64 bytes, the swizzle width) x box_rows rows of one piece
+// (SW_BYTES, the swizzle width) x box_rows rows of one piece
 static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kpad, int npieces,
-                    int box_rows) {
+                    int box_rows, int box_k = TK) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return -1;
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)npieces};
   cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
-  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     fprintf(stderr, "hotrg: tensor map encoding failed (CUresult %d; rows %d, kpad %d)\n", (int)r, rows,
@@ -478,6 +769,18 @@ static bool gemm_smem_attr_set() {
   return true;
 }
 
+static bool pair_smem_attr_set() {
+  static std::atomic<int> done[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return true;
+  if (cudaFuncSetAttribute(tc_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) !=
+      cudaSuccess)
+    return false;
+  if (dev >= 0 && dev < kMaxDevices) done[dev].store(1, std::memory_order_release);
+  return true;
+}
+
 int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
                    int npieces, int nterms, const int* pa, const int* pb, float* C, long long ldc,
                    int* err_flag, cudaStream_t s, float* ms_out) {
@@ -494,8 +797,13 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
       return -1;
     }
   }
+  const bool use_pair = HOTRG_TC_USE_PAIR != 0 && Kpad % P_TK == 0;
   CUtensorMap ma, mb;
-  if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) return -1;
+  if (use_pair) {
+    if (make_map(&ma, A, M, Kpad, npieces, 128, P_TK) || make_map(&mb, B, N, Kpad, npieces, 128, P_TK)) return -1;
+  } else if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) {
+    return -1;
+  }
   // terms ordered by decreasing piece order (pa + pb): the smallest terms go first into
   // the zeroed accumulator of a chunk, the leading term x_0 y_0 last
   TcTerms terms;
@@ -516,19 +824,24 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
     terms.code |= (unsigned long long)(a | (b << 2)) << (4 * t);
     if (a + b > 0) terms.nsmall = t + 1;
   }
-  if (!gemm_smem_attr_set()) {
+  if (use_pair ? !pair_smem_attr_set() : !gemm_smem_attr_set()) {
     fprintf(stderr, "hotrg: GEMM shared-memory attribute refused\n");
     return -1;
   }
   const long long ntiles = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-  const int grid = (int)std::min<long long>(ntiles, sm_count());
+  const long long ngroups = (long long)((M + 255) / 256) * ((N + 255) / 256);
+  const int grid = use_pair ? 2 * (int)std::min<long long>(ngroups, std::max(1, sm_count() / 2))
+                            : (int)std::min<long long>(ntiles, sm_count());
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ms_out) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, Kpad / TK, terms, err_flag);
+  if (use_pair)
+    tc_gemm_pair_kernel<<<grid, P_NTHREADS, P_SMEM, s>>>(ma, mb, C, M, N, ldc, Kpad / P_TK, terms, err_flag);
+  else
+    tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, Kpad / TK, terms, err_flag);
   ++g_launches;
   if (ms_out) {
     cudaEventRecord(e1, s);
