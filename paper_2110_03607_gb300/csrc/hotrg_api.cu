@@ -1421,8 +1421,15 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
       while (hmap.size() % 4) hmap.push_back(0);
       return off;
     };
+    // Each parity's list runs over the last slot's index slowest (any order serves, as
+    // long as the A blocks, the B blocks and the C rows share it): in this order the
+    // consecutive list positions that the lanes of a warp take in the last prime stage
+    // share the hat index of the last leg, so they read one isometry row
     std::vector<int> rowblk(R), rowpos(R), kmap[2];
-    for (long long r = 0; r < R; ++r) {
+    const int chi_last = c->chis[to[d - 1]];
+    const long long rest = R / chi_last;
+    for (long long o = 0; o < R; ++o) {
+      const long long r = (o % rest) * chi_last + o / rest;
       long long idx = r;
       int p_ = 0;
       for (int k = d - 1; k >= 0; --k) {

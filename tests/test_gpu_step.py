@@ -363,3 +363,21 @@ def test_ising3d_chi16_restart_one_step_against_full_oracle_step(pkg, chi16_rest
                 assert np.all(dev <= col_tol), (f"step 5 leg {leg.axis}", dev, col_tol)
     finally:
         pkg.hotrg_free(ctx)
+
+
+def test_ising3d_chi20_free_energy_matches_oracle_reference(pkg):
+    # the precision sweep's larger bond dimension: 3D Ising chi = 20 at beta_c, the oracle's
+    # reference through step 7 (steps 5-7 have every bond at 20), BF16X6 with Z2 blocks
+    gold = _golden("ising3d_chi20")
+    assert max(gold) >= 7
+    g = pkg.Hotrg(3, 0.2216544, 0.0, precision=pkg.PREC_BF16X6, z2=True)
+    try:
+        for step in range(1, max(gold) + 1):
+            g.step((2 + step - 1) % 3, 20)
+            lnz, _ = g.free_energy()
+            ref = gold[step]["ln_z_per_site"]
+            assert abs(lnz - ref) / abs(ref) <= 1e-7, (step, lnz, ref)
+            if step >= 4:   # every steady step contracted in the split form
+                assert not pkg.hotrg_step_times(g.ctx)[2], step
+    finally:
+        g.close()
