@@ -777,7 +777,8 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   // K is too short), pick the one that minimises (CTAs on the busiest SM) x (K per CTA
   // + a fixed cost).
   auto gram_splits = [&](long long m, long long K) {
-    const long long ut = ((m + 63) / 64) * ((m + 63) / 64 + 1) / 2;
+    const long long tl = gram_tile();
+    const long long ut = ((m + tl - 1) / tl) * ((m + tl - 1) / tl + 1) / 2;
     const long long sms = num_sms();
     int best = 1, best_any = 1;
     double best_cost = 1e300, best_any_cost = 1e300;

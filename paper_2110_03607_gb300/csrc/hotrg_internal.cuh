@@ -82,6 +82,8 @@ void launch_scale(const double* in, double* out, long long n, const DevState* st
 // ---- kernels_env.cu
 // FP64 FMA rate of the current device in TFLOP/s (CUDA events; 0 or a negative status)
 int measure_fp64_rate(double* tflops);
+// edge of the tiles of the symmetric (upper_only) FP64 products
+int gram_tile();
 // returns the number of split-K partials written
 int launch_gemm_nt_f64(const double* A, long long lda, const double* B, long long ldb,
                        double* C, long long ldc, long long split_stride,

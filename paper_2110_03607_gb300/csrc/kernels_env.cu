@@ -13,19 +13,25 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 }
 
-// C[z][i][j] = sum_{k in split z} A[i*lda + k] * B[j*ldb + k]
-__global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
+// C[z][i][j] = sum_{k in split z} A[i*lda + k] * B[j*ldb + k], in T x T tiles (T = 64 for
+// the large products, 32 for the symmetric Gram blocks, whose diagonal tiles are half
+// wasted and whose sizes sit just above multiples of 64 at zero field); 256 threads,
+// (T/16) x (T/16) outputs each.
+template <int T>
+__global__ void __launch_bounds__(256, 2) gemm_nt_f64_kernel(
     const double* __restrict__ A, long long lda, const double* __restrict__ B, long long ldb,
     double* __restrict__ C, long long ldc, long long split_stride, int M, int N, long long K,
     long long kchunk, int upper_only) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  constexpr int R = T / 16;      // outputs per thread along each dim
+  constexpr int L = T / 16;      // consecutive k loaded per thread per operand
+  __shared__ double As[BK][T + 1];
+  __shared__ double Bs[BK][T + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   int bx = blockIdx.x, by = blockIdx.y;
   if (upper_only) {
     // blockIdx.x enumerates the tile pairs (ti <= tj) of the upper triangle, row by row
-    const int nt = (M + BM - 1) / BM;
+    const int nt = (M + T - 1) / T;
     int t = blockIdx.x, ti = 0;
     while (t >= nt - ti) {
       t -= nt - ti;
@@ -34,23 +40,24 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
     by = ti;
     bx = ti + t;
   }
-  const int n0 = bx * BN, m0 = by * BM;
+  const int n0 = bx * T, m0 = by * T;
   const long long k_lo = (long long)blockIdx.z * kchunk;
   long long k_hi = k_lo + kchunk;
   if (k_hi > K) k_hi = K;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  // loader mapping: 64 rows x 16 k; thread -> (row = tid / 4, k = (tid % 4) * 4 .. +3).
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
+  // loader mapping: T rows x 16 k; thread -> (row = tid / (16 / L), k = (tid % (16 / L)) * L .. +L-1).
   // The next slab is fetched into registers while the current one is multiplied.
-  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  constexpr int TPR = 16 / L;    // threads per row
+  const int lr = tid / TPR, lk = (tid % TPR) * L;
   const int ra = m0 + lr, rb = n0 + lr;
-  double pa[4], pb[4];
+  double pa[L], pb[L];
   auto fetch = [&](long long k0) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < L; ++u) {
       long long k = k0 + lk + u;
       pa[u] = (ra < M && k < k_hi) ? A[(long long)ra * lda + k] : 0.0;
       pb[u] = (rb < N && k < k_hi) ? B[(long long)rb * ldb + k] : 0.0;
@@ -59,7 +66,7 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
   if (k_lo < k_hi) fetch(k_lo);
   for (long long k0 = k_lo; k0 < k_hi; k0 += BK) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < L; ++u) {
       As[lk + u][lr] = pa[u];
       Bs[lk + u][lr] = pb[u];
     }
@@ -67,30 +74,32 @@ __global__ void __launch_bounds__(256) gemm_nt_f64_kernel(
     if (k0 + BK < k_hi) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
   double* Cz = C + (long long)blockIdx.z * split_stride;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     int r = m0 + ty + 16 * i;
     if (r >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       int c = n0 + tx + 16 * j;
       if (c < N) Cz[(long long)r * ldc + c] = acc[i][j];
     }
   }
 }
+
+int gram_tile() { return 32; }
 
 // Returns the number of split-K partial products written (nsplit after rounding the
 // K chunk up to a multiple of BK): the partials a reduction must read.
@@ -102,11 +111,15 @@ int launch_gemm_nt_f64(const double* A, long long lda, const double* B, long lon
   kchunk = (kchunk + BK - 1) / BK * BK;
   nsplit = (int)((K + kchunk - 1) / kchunk);
   if (nsplit < 1) nsplit = 1;
-  const int nt = (M + BM - 1) / BM;
-  dim3 grid = upper_only ? dim3(nt * (nt + 1) / 2, 1, nsplit)
-                         : dim3((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
-  gemm_nt_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, split_stride, M, N, K, kchunk,
-                                           upper_only);
+  if (upper_only) {   // symmetric Grams: the upper triangle of 32 x 32 tiles
+    constexpr int T = 32;
+    const int nt = (M + T - 1) / T;
+    gemm_nt_f64_kernel<T><<<dim3(nt * (nt + 1) / 2, 1, nsplit), 256, 0, s>>>(A, lda, B, ldb, C, ldc,
+                                                                            split_stride, M, N, K, kchunk, 1);
+  } else {
+    gemm_nt_f64_kernel<BM><<<dim3((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit), 256, 0, s>>>(
+        A, lda, B, ldb, C, ldc, split_stride, M, N, K, kchunk, 0);
+  }
   ++g_launches;
   return nsplit;
 }
