@@ -831,9 +831,9 @@ def main():
                 "peak_source": "FP64 FMA rate measured in this run (hotrg_fp64_rate)"}
     else:
         # DRAM bytes (read + write) of one Z2 block GEMM launch from the ncu capture in
-        # profiles/tc_gemm_kernel_ising3d_chi16_bf16x6.md (launch shape of the first steady
-        # steps: M = K = 2048, N = 32768); only for that workload and form
-        traffic = (0.655e9 + 0.302e9) if (WORKLOAD == "ising3d_chi16" and args.precision == "bf16x6"
+        # profiles/tc_gemm_pair_kernel_ising3d_chi16_bf16x6.md (the block shape of the first
+        # steady steps: M = K = 2048, N = 32768); only for that workload and form
+        traffic = (0.587e9 + 0.246e9) if (WORKLOAD == "ising3d_chi16" and args.precision == "bf16x6"
                                           and args.z2 == "on") else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
