@@ -41,8 +41,10 @@ struct URow<float, NN> {
   }
 };
 
+// The stages that read the Z2 blocks of C and write those of B are held to three and
+// four CTAs per SM (80 and 64 registers): both are bound by memory latency
 template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
-__global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
+__global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
                                                     const TAcc* __restrict__ U, void* out, Z2In zi,
                                                     Z2Out zo) {
   extern __shared__ __align__(16) unsigned char smem_u[];
@@ -184,8 +186,9 @@ __global__ void __launch_bounds__(256) chain_kernel(ChainDesc d, const TIn* __re
       const long long row0 = out_off / zo.kpad;
       const int kb = kidx >= zo.rb0 ? 1 : 0;
       const long long kpos = (long long)(kb ? kidx - zo.rb0 : kidx);
-      __nv_bfloat16* ob = zo.blk[kb] + kpos;
-      const long long ld = zo.ld[kb], ps = zo.pstride[kb];
+      // selects, not an index: an indexed parameter array would be copied to local memory
+      __nv_bfloat16* ob = (kb ? zo.blk[1] : zo.blk[0]) + kpos;
+      const long long ld = kb ? zo.ld[1] : zo.ld[0], ps = kb ? zo.pstride[1] : zo.pstride[0];
 #pragma unroll
       for (int n = 0; n < NN; ++n) {
         if (n >= d.nn) break;
