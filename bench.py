@@ -1,6 +1,6 @@
 """Benchmark: HOTRG coarse-graining steps/s on one GB300 (per rank).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|tf32x3|tf32|fp64]
                     [--workload ising3d_chi16|ising3d_chi20|ising4d_chi6|ising4d_chi13|ising4d_chi14|
                                 batch3d_mixed|energy3d_chi12|energy3d_chi12_scan]
                     [--z2 on|off] [--impl ours|reference]
@@ -112,6 +112,22 @@ def select_workload(name):
 
 def axes_for(n):
     return [(FIRST_AXIS + s) % D for s in range(n)]
+
+
+# --precision: binding constant, piece products (terms) per algorithmic product, the
+# tensor-core rate of the piece type relative to BF16 (TF32 at the recipe's nominal
+# 1.1 / 2.25 PFLOP/s dense), and the JSON dtype
+PRECISIONS = {
+    "bf16x6": ("PREC_BF16X6", 6, 1.0, "bf16x6-split/fp32-acc; f64 env, eig, lnZ"),
+    "bf16x3": ("PREC_BF16X3", 3, 1.0, "bf16x3-split/fp32-acc; f64 env, eig, lnZ"),
+    "tf32x3": ("PREC_TF32X3", 3, 1.1 / 2.25, "tf32x3-split/fp32-acc; f64 env, eig, lnZ"),
+    "tf32": ("PREC_TF32", 1, 1.1 / 2.25, "tf32/fp32-acc; f64 env, eig, lnZ"),
+    "fp64": ("PREC_FP64", 1, None, "f64"),
+}
+
+
+def prec_const(pkg, name):
+    return getattr(pkg, PRECISIONS[name][0])
 
 
 def load_peaks():
@@ -333,7 +349,7 @@ def batch_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    prec = prec_const(pkg, args.precision)
     inst = batch_instances()
     n = len(inst)
     streams = [torch.cuda.Stream() for _ in range(n)]
@@ -427,9 +443,7 @@ def batch_arm(args):
             "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
-                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ",
-                      "fp64": "f64"}[args.precision],
+            "dtype": PRECISIONS[args.precision][3],
             "data": "synthetic (Ising initial tensors from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, {K} timed batch steps",
@@ -476,7 +490,7 @@ def energy_arm(args):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
-    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    prec = prec_const(pkg, args.precision)
     g = pkg.Hotrg(D, BETA, H, precision=prec)
     pkg.hotrg_set_tangent(g.ctx, True)
     for a in axes[: GROWTH_STEPS + args.warmup]:
@@ -537,11 +551,12 @@ def energy_arm(args):
                 "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
     else:
         peaks, peak_src = load_peaks()
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        nterms = 6 if args.precision == "bf16x6" else 3
+        _, nterms, rate, _ = PRECISIONS[args.precision]
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * rate
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                "peak_source": f"bf16_tflops_sustained of {peak_src}"
+                               + ("" if rate == 1.0 else f" x {rate:.4f} (TF32 / BF16 nominal dense rate)"),
                 "issued_tflops": achieved * nterms if achieved else None,
                 "issued_frac": achieved * nterms / peak if achieved else None}
     roof["note"] = ("bottleneck region per c'-slice: three GEMMs of 2 R^2 Nc flops "
@@ -552,8 +567,7 @@ def energy_arm(args):
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
-                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ", "fp64": "f64"}[args.precision],
+            "dtype": PRECISIONS[args.precision][3],
             "data": "synthetic (Ising initial tensor and its beta-derivative from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, steps {GROWTH_STEPS + args.warmup + 1}-"
@@ -604,7 +618,7 @@ def energy_scan_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    prec = prec_const(pkg, args.precision)
     betas = [0.21 + 0.02 * i / 31.0 for i in range(32)]
     n = len(betas)
     streams = [torch.cuda.Stream() for _ in range(n)]
@@ -667,8 +681,7 @@ def energy_scan_arm(args):
             "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
-                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ", "fp64": "f64"}[args.precision],
+            "dtype": PRECISIONS[args.precision][3],
             "data": "synthetic (Ising initial tensors and their beta-derivatives from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, {K} timed batch steps",
@@ -702,7 +715,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="bf16x6", choices=list(PRECISIONS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -738,7 +751,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = {"bf16x6": pkg.PREC_BF16X6, "bf16x3": pkg.PREC_BF16X3, "fp64": pkg.PREC_FP64}[args.precision]
+    prec = prec_const(pkg, args.precision)
     stream = torch.cuda.current_stream()
 
     g = pkg.Hotrg(D, BETA, H, precision=prec, z2=args.z2 == "on")
@@ -821,9 +834,9 @@ def main():
     bn_launches = launch_sum.get("bottleneck", 0)
     bn_ms = phase_bn_ms / max(1, bn_launches)
     flops_per_launch = bn_done / max(1, bn_launches)
-    nterms = {"bf16x6": 6, "bf16x3": 3, "fp64": 1}[args.precision]
+    _, nterms, rate, _ = PRECISIONS[args.precision]
     achieved = flops_per_launch / (bn_ms / 1000.0) / 1e12 if bn_ms > 0 else None
-    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * (rate or 1.0)
     if args.precision == "fp64":
         fp64_peak = pkg.hotrg_fp64_rate()
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -839,7 +852,8 @@ def main():
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_note": "bytes per launch at the step-4..7 launch shape (M=K=2048, N=32768); "
                                 "later steps have unequal blocks" if traffic else None,
-                "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                "peak_source": f"bf16_tflops_sustained of {peak_src}"
+                               + ("" if rate == 1.0 else f" x {rate:.4f} (TF32 / BF16 nominal dense rate)"),
                 "issued_tflops": achieved * nterms if achieved else None,
                 "issued_frac": achieved * nterms / peak if achieved else None,
                 "algorithmic_flops_per_launch": flops_per_launch,
@@ -902,9 +916,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16x6": "bf16x6-split/fp32-acc; f64 env, eig, lnZ",
-                      "bf16x3": "bf16x3-split/fp32-acc; f64 env, eig, lnZ",
-                      "fp64": "f64"}[args.precision],
+            "dtype": PRECISIONS[args.precision][3],
             "data": "synthetic (Ising initial tensor from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, "

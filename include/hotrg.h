@@ -60,12 +60,17 @@ enum hotrg_status {
 /* Arithmetic of the contractions (prime chain, bottleneck, non-prime chain).
  * The environment matrices, the eigen-solver and the ln Z accumulation are
  * FP64 in every mode.  BF16X3: operands split into 2 BF16 pieces, 3 piece
- * products, FP32 accumulation.  BF16X6: 3 pieces, 6 products.  FP64: plain
- * FP64 everywhere. */
+ * products, FP32 accumulation.  BF16X6: 3 pieces, 6 products.  TF32: one TF32
+ * piece (10 stored mantissa bits, rounded to nearest), one product.  TF32X3: 2
+ * TF32 pieces, 3 products.  The tensor cores take TF32 at half the BF16 rate,
+ * so TF32X3 issues as much tensor time as BF16X6.  FP64: plain FP64
+ * everywhere. */
 enum hotrg_precision {
   HOTRG_PREC_FP64 = 0,
   HOTRG_PREC_BF16X3 = 1,
-  HOTRG_PREC_BF16X6 = 2
+  HOTRG_PREC_BF16X6 = 2,
+  HOTRG_PREC_TF32 = 3,
+  HOTRG_PREC_TF32X3 = 4
 };
 
 /* Start a run from the Ising initial tensor of Sec. 2, Eq. (2.4):
@@ -306,7 +311,8 @@ int hotrg_tensor(hotrg_ctx* ctx, double* T, int64_t cap, int dims[8]);
 /* The bottleneck contraction of Eq. (BottleneckPart) on its own:
  * C[M][N] = sum_k A[M][K] B[N][K] (both operands K-contiguous, row-major,
  * FP64 in and out) computed with the kernels of precision `mode` (split-BF16
- * pieces on the tensor cores with FP32 accumulation, or FP64 DFMA tiles).
+ * or split-TF32 pieces on the tensor cores with FP32 accumulation, or FP64
+ * DFMA tiles).
  * A, B, C may be host or device pointers.  Synchronous; allocates and frees
  * its own device scratch.  1 <= M, N, K <= 2^20 and M*K, N*K, M*N <= 2^31.
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
@@ -326,7 +332,9 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
  * the scratch is 256 + r(2*np*M*Kp) + r(2*np*N*Kp) + r(4*M*N) bytes, with
  * np = 2 (BF16X3) or 3 (BF16X6), Kp = K rounded up to a multiple of 64 and
  * r(x) = x rounded up to a multiple of 256; sizes whose scratch exceeds the
- * array are rejected with HOTRG_EINVAL (the FP64 mode needs no scratch).  The
+ * array are rejected with HOTRG_EINVAL (the FP64 mode needs no scratch).
+ * mode is HOTRG_PREC_FP64, HOTRG_PREC_BF16X3 or HOTRG_PREC_BF16X6 (the TF32
+ * modes give HOTRG_EINVAL here).  The
  * size limits of hotrg_gemm_nt apply in every mode.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Work is enqueued on
@@ -340,12 +348,12 @@ int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double* A, const 
                           double* C, void* stream);
 
 /* Rate probe of the bottleneck GEMM kernel alone: allocates operand pieces of
- * an M x K and an N x K operand (BF16-exact values) and an FP32 product on the
- * current device, launches the split-BF16 tensor-core GEMM of hotrg_gemm_nt
- * once to warm up, then `iters` times back to back on the legacy default
- * stream, and returns the mean milliseconds per launch (CUDA events).  For
- * rooflines and tuning; the paper has no counterpart.  mode is
- * HOTRG_PREC_BF16X3 or HOTRG_PREC_BF16X6.  Errors: EINVAL, ENOMEM, ECUDA,
+ * an M x K and an N x K operand (values exact in BF16 and TF32) and an FP32
+ * product on the current device, launches the split tensor-core GEMM of
+ * hotrg_gemm_nt once to warm up, then `iters` times back to back on the legacy
+ * default stream, and returns the mean milliseconds per launch (CUDA events).
+ * For rooflines and tuning; the paper has no counterpart.  mode is any split
+ * mode (BF16X3, BF16X6, TF32, TF32X3).  Errors: EINVAL, ENOMEM, ECUDA,
  * ETIMEOUT. */
 int hotrg_gemm_rate(int mode, int M, int N, int K, int iters, double* ms_per_launch);
 

@@ -19,6 +19,8 @@ _LIB = None
 PREC_FP64 = 0
 PREC_BF16X3 = 1
 PREC_BF16X6 = 2
+PREC_TF32 = 3
+PREC_TF32X3 = 4
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -360,7 +362,8 @@ def hotrg_shard_finish(ctx, axis: int, chi: int, slices):
 
 
 def hotrg_gemm_rate(mode: int, m: int, n: int, k: int, iters: int) -> float:
-    """Milliseconds per launch of the split-BF16 GEMM kernel on device-resident operands."""
+    """Milliseconds per launch of the split GEMM kernel (BF16 or TF32 pieces of `mode`) on
+    device-resident operands."""
     v = ctypes.c_double()
     _check(load().hotrg_gemm_rate(mode, m, n, k, iters, ctypes.byref(v)), "hotrg_gemm_rate")
     return v.value

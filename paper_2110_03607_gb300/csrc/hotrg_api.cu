@@ -115,6 +115,7 @@ bool make_stage(ChainDesc& d, const View& in, const View& out, int a_name, int b
   d.nn = nn;
   d.ldu = nn;
   d.npieces = 1;
+  d.pfmt = PIECE_BF16;
   if (d.total >= (1LL << 32)) return false;
   for (int k = 0; k < d.ndim; ++k) {
     // Hacker's Delight unsigned division by an invariant: l = ceil(log2 s),
@@ -627,7 +628,7 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
 }
 
 int hotrg_set_precision(hotrg_ctx* c, int mode) {
-  if (!c || mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6) return HOTRG_EINVAL;
+  if (!c || mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_TF32X3) return HOTRG_EINVAL;
   if (mode != HOTRG_PREC_FP64 && !tc_gemm_ready()) return HOTRG_ECUDA;
   c->precision = mode;
   return HOTRG_OK;
@@ -1358,7 +1359,9 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   if (phase == PH_FINISH && (!sh.in || sh.cap != (long long)chi_c * slice_elems)) return HOTRG_EINVAL;
   if (phase == PH_FULL || phase == PH_CONTRACT) {
   const long long Ns = Pn * P;            // columns of the bottleneck per slice: (n', n~)
-  const int npieces = c->precision == HOTRG_PREC_BF16X3 ? 2 : 3;
+  const int npieces = split_pieces(c->precision);
+  const int pfmt = split_format(c->precision);
+  const long long pbytes = piece_bytes(pfmt);
   const long long Kpad = fp64 ? R : (R + 63) / 64 * 64;
   // chain intermediates
   long long chain_max = 1;
@@ -1387,7 +1390,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     // more chain buffers
     const double per_unit =
         (z2 ? 1.6 : 1.0) * (tangent ? (fp64 ? 3.0 : 4.0) : 1.0) * (double)(Ns / nnew1) *
-            ((fp64 ? 8.0 * R : 2.0 * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
+            ((fp64 ? 8.0 * R : (double)pbytes * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
         (tangent ? 5.0 : 2.0) * (double)elt * (double)chain_max / nnew1;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -1530,13 +1533,13 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     }
   } else {
     if (!zfold) {   // with the Z2 blocks the last prime stage writes the B blocks directly
-      CHECK_ALLOC(dev_alloc(c, c->Bp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
-      if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
+      CHECK_ALLOC(dev_alloc(c, c->Bp, pbytes * npieces * Nsub * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->Bp.p, 0, pbytes * npieces * Nsub * Kpad, s);
       CHECK_ALLOC(dev_alloc(c, c->Cb, sizeof(float) * R * Nsub));
     }
     if (tangent) {
-      CHECK_ALLOC(dev_alloc(c, c->dBp, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad));
-      if (Kpad != R) cudaMemsetAsync(c->dBp.p, 0, sizeof(__nv_bfloat16) * npieces * Nsub * Kpad, s);
+      CHECK_ALLOC(dev_alloc(c, c->dBp, pbytes * npieces * Nsub * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->dBp.p, 0, pbytes * npieces * Nsub * Kpad, s);
       CHECK_ALLOC(dev_alloc(c, c->dB64, sizeof(double) * Nsub * R));
       CHECK_ALLOC(dev_alloc(c, c->tBp, sizeof(double) * Nsub * R));
       CHECK_ALLOC(dev_alloc(c, c->dCb, sizeof(float) * R * Nsub));
@@ -1544,22 +1547,22 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     }
     Phase ph(c, 4);
     if (z2) {
-      CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(__nv_bfloat16) * npieces * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
-      CHECK_ALLOC(dev_alloc(c, c->Zb, sizeof(__nv_bfloat16) * npieces * maxL * (Kpb[0] + Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Za, pbytes * npieces * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
+      CHECK_ALLOC(dev_alloc(c, c->Zb, pbytes * npieces * maxL * (Kpb[0] + Kpb[1])));
       CHECK_ALLOC(dev_alloc(c, c->Zc, sizeof(float) * R * ldz));
-      __nv_bfloat16* za = (__nv_bfloat16*)c->Za.p;
+      char* za = (char*)c->Za.p;
       launch_z2_gather_split(Tc, R, zmap + moff_k[0], (int)Rb[0], zmap + moff_k[0], (int)Kpb[0], za,
-                             Rb[0] * Kpb[0], npieces, s);
+                             Rb[0] * Kpb[0], npieces, pfmt, s);
       launch_z2_gather_split(Tc, R, zmap + moff_k[1], (int)Rb[1], zmap + moff_k[1], (int)Kpb[1],
-                             za + npieces * Rb[0] * Kpb[0], Rb[1] * Kpb[1], npieces, s);
+                             za + pbytes * npieces * Rb[0] * Kpb[0], Rb[1] * Kpb[1], npieces, pfmt, s);
     } else {
-      CHECK_ALLOC(dev_alloc(c, c->Ap, sizeof(__nv_bfloat16) * npieces * R * Kpad));
-      if (Kpad != R) cudaMemsetAsync(c->Ap.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
-      launch_split_bf16(Tc, R, R, R, (__nv_bfloat16*)c->Ap.p, Kpad, R * Kpad, npieces, s);
+      CHECK_ALLOC(dev_alloc(c, c->Ap, pbytes * npieces * R * Kpad));
+      if (Kpad != R) cudaMemsetAsync(c->Ap.p, 0, pbytes * npieces * R * Kpad, s);
+      launch_split(Tc, R, R, R, c->Ap.p, Kpad, R * Kpad, npieces, pfmt, s);
       if (tangent) {
-        CHECK_ALLOC(dev_alloc(c, c->dAp, sizeof(__nv_bfloat16) * npieces * R * Kpad));
-        if (Kpad != R) cudaMemsetAsync(c->dAp.p, 0, sizeof(__nv_bfloat16) * npieces * R * Kpad, s);
-        launch_split_bf16((const double*)c->dT.p, R, R, R, (__nv_bfloat16*)c->dAp.p, Kpad, R * Kpad, npieces, s);
+        CHECK_ALLOC(dev_alloc(c, c->dAp, pbytes * npieces * R * Kpad));
+        if (Kpad != R) cudaMemsetAsync(c->dAp.p, 0, pbytes * npieces * R * Kpad, s);
+        launch_split((const double*)c->dT.p, R, R, R, c->dAp.p, Kpad, R * Kpad, npieces, pfmt, s);
       }
     }
   }
@@ -1575,22 +1578,8 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     for (int l = k + 1; l < d; ++l) p_ *= arr[l];
     return p_;
   };
-  int terms_a[6], terms_b[6], nterms;
-  if (npieces == 2) {
-    int ta[3] = {1, 0, 0}, tb[3] = {0, 1, 0};
-    nterms = 3;
-    for (int t = 0; t < 3; ++t) {
-      terms_a[t] = ta[t];
-      terms_b[t] = tb[t];
-    }
-  } else {
-    int ta[6] = {2, 1, 0, 1, 0, 0}, tb[6] = {0, 1, 2, 0, 1, 0};
-    nterms = 6;
-    for (int t = 0; t < 6; ++t) {
-      terms_a[t] = ta[t];
-      terms_b[t] = tb[t];
-    }
-  }
+  int terms_a[6], terms_b[6];
+  const int nterms = split_terms(npieces, terms_a, terms_b);
 
   const void* cblk_cur[2] = {nullptr, nullptr};   // this sub-slice's C blocks (Z2)
   for (int sl = sl_lo; sl < sl_hi; ++sl)
@@ -1647,6 +1636,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         }
       } else if (c->f64_chains && !tangent) {
         cd.npieces = npieces;
+        cd.pfmt = pfmt;
         cd.piece_stride = Nc * Kpad;
         launch_chain_f64acc(cd, src, src_f64, (const double*)c->U64.p + u_off[j] + ucol, dst,
                             last ? OUT_BF16_SPLIT : OUT_F64, s);
@@ -1654,6 +1644,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         // straight into the Z2 blocks of B: the outputs whose column parity matches
         // the parity of their k, at the positions the bottleneck's blocks use
         cd.npieces = npieces;
+        cd.pfmt = pfmt;
         const Z2Chunk& ch = zch[n1lo / n1_chunk];
         const int q = c->par[to[0]][sl];
         Z2Out zo;
@@ -1667,15 +1658,14 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         zo.nrow_step = cd.n_out_stride / Kpad;
         for (int b = 0; b < 2; ++b) {
           const long long Nb = ch.L[b ^ q];
-          __nv_bfloat16* zb = (__nv_bfloat16*)c->Zb.p + npieces * (b == 0 ? 0 : maxL * Kpb[0]);
+          char* zb = (char*)c->Zb.p + pbytes * npieces * (b == 0 ? 0 : maxL * Kpb[0]);
           zo.blk[b] = zb;
           zo.ld[b] = Kpb[b];
           zo.pstride[b] = Nb * Kpb[b];
           // the K padding of every row (of every piece) reads as zero
           if (Kpb[b] > Rb[b] && Nb > 0 &&
-              cudaMemset2DAsync(zb + Rb[b], sizeof(__nv_bfloat16) * Kpb[b], 0,
-                                sizeof(__nv_bfloat16) * (Kpb[b] - Rb[b]), (size_t)npieces * Nb, s) !=
-                  cudaSuccess)
+              cudaMemset2DAsync(zb + pbytes * Rb[b], pbytes * Kpb[b], 0, pbytes * (Kpb[b] - Rb[b]),
+                                (size_t)npieces * Nb, s) != cudaSuccess)
             return cuda_status(c) == HOTRG_OK ? (c->poisoned = HOTRG_ECUDA) : HOTRG_ECUDA;
         }
         {
@@ -1695,6 +1685,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         launch_chain_f32_z2out(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, zo, s);
       } else {
         cd.npieces = npieces;
+        cd.pfmt = pfmt;
         cd.piece_stride = Nc * Kpad;
         launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, dst,
                          last ? OUT_BF16_SPLIT : OUT_F32, s);
@@ -1718,8 +1709,8 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
           launch_chain_f32(cdt, dsrc, src_f64, (const float*)c->U32.p + u_off[j] + ucol, ddst, mode, s);
           launch_chain_f32(cdt, src, src_f64, (const float*)c->dU32.p + u_off[j] + ucol, tdst, mode, s);
           if (last) {   // dB = both terms, summed in FP64 as they are split
-            launch_split_bf16((const double*)ddst, Nc, R, R, (__nv_bfloat16*)c->dBp.p, Kpad, Nc * Kpad, npieces,
-                              s, (const double*)tdst);
+            launch_split((const double*)ddst, Nc, R, R, c->dBp.p, Kpad, Nc * Kpad, npieces, pfmt, s,
+                         (const double*)tdst);
           } else {
             launch_add_f32((const float*)tdst, (float*)ddst, view_elems(out), s);
           }
@@ -1758,17 +1749,17 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
                              (int)Nb, Kpb[b], 1, 0, s);
           cblk[b] = zc;
         } else {
-          __nv_bfloat16* zb = (__nv_bfloat16*)c->Zb.p + npieces * b_off;
+          char* zb = (char*)c->Zb.p + pbytes * npieces * b_off;
           float* zc = (float*)c->Zc.p + c_off;
           if (!zfold) {   // else the last prime stage wrote the block
             Phase pg(c, 11);
-            launch_z2_gather_bf16((const __nv_bfloat16*)c->Bp.p, Kpad, Nc * Kpad, nmap, (int)Nb, kmap,
-                                  (int)Kpb[b], zb, Nb * Kpb[b], npieces, s);
+            launch_z2_gather_pieces(c->Bp.p, Kpad, Nc * Kpad, nmap, (int)Nb, kmap, (int)Kpb[b], zb,
+                                    Nb * Kpb[b], npieces, pfmt, s);
           }
           Phase ph(c, 6);
-          if (launch_tc_gemm((const __nv_bfloat16*)c->Za.p + npieces * a_off, (int)Rb[b], zb, (int)Nb,
+          if (launch_tc_gemm((const char*)c->Za.p + pbytes * npieces * a_off, (int)Rb[b], zb, (int)Nb,
                              (int)Kpb[b], npieces, nterms, terms_a, terms_b, zc, ldz,
-                             &((DevState*)c->state.p)->status, s, nullptr) != 0)
+                             &((DevState*)c->state.p)->status, s, nullptr, pfmt) != 0)
             return launch_failed(c, "tensor-core GEMM (Z2 block)", Rb[b], Nb, Kpb[b]);
           cblk[b] = zc;
         }
@@ -1801,17 +1792,14 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         launch_axpby(1.0, (const double*)c->tCb.p, 1.0, (double*)c->dCb.p, R * Nc, s);
       }
     } else {
-      if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
-                         (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->Cb.p, Nc,
-                         &((DevState*)c->state.p)->status, s, nullptr) != 0)
+      if (launch_tc_gemm(c->Ap.p, (int)R, c->Bp.p, (int)Nc, (int)Kpad, npieces, nterms, terms_a, terms_b,
+                         (float*)c->Cb.p, Nc, &((DevState*)c->state.p)->status, s, nullptr, pfmt) != 0)
         return launch_failed(c, "tensor-core GEMM", R, Nc, Kpad);
       if (tangent) {   // dC = T^ . dB^T + dT^ . B^T
-        if (launch_tc_gemm((const __nv_bfloat16*)c->Ap.p, (int)R, (const __nv_bfloat16*)c->dBp.p, (int)Nc,
-                           (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->dCb.p, Nc,
-                           &((DevState*)c->state.p)->status, s, nullptr) != 0 ||
-            launch_tc_gemm((const __nv_bfloat16*)c->dAp.p, (int)R, (const __nv_bfloat16*)c->Bp.p, (int)Nc,
-                           (int)Kpad, npieces, nterms, terms_a, terms_b, (float*)c->tCb.p, Nc,
-                           &((DevState*)c->state.p)->status, s, nullptr) != 0)
+        if (launch_tc_gemm(c->Ap.p, (int)R, c->dBp.p, (int)Nc, (int)Kpad, npieces, nterms, terms_a, terms_b,
+                           (float*)c->dCb.p, Nc, &((DevState*)c->state.p)->status, s, nullptr, pfmt) != 0 ||
+            launch_tc_gemm(c->dAp.p, (int)R, c->Bp.p, (int)Nc, (int)Kpad, npieces, nterms, terms_a, terms_b,
+                           (float*)c->tCb.p, Nc, &((DevState*)c->state.p)->status, s, nullptr, pfmt) != 0)
           return launch_failed(c, "tensor-core GEMM (derivative)", R, Nc, Kpad);
         launch_add_f32((const float*)c->tCb.p, (float*)c->dCb.p, R * Nc, s);
       }
@@ -2108,14 +2096,15 @@ int hotrg_tensor(hotrg_ctx* c, double* T, int64_t cap, int dims[8]) {
 }
 
 int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* B, double* C) {
-  if (mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_BF16X6 || M < 1 || N < 1 || K < 1 ||
+  if (mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_TF32X3 || M < 1 || N < 1 || K < 1 ||
       M > (1 << 20) || N > (1 << 20) || K > (1 << 20) || !A || !B || !C)
     return HOTRG_EINVAL;
   if ((long long)M * K > (1LL << 31) || (long long)N * K > (1LL << 31) || (long long)M * N > (1LL << 31))
     return HOTRG_EINVAL;
   if (mode != HOTRG_PREC_FP64 && !tc_gemm_ready()) return HOTRG_ECUDA;
   cudaStream_t s = nullptr;
-  const int np = mode == HOTRG_PREC_BF16X3 ? 2 : 3;
+  const int np = split_pieces(mode), pfmt = split_format(mode);
+  const long long pbytes = piece_bytes(pfmt);
   const long long Kpad = mode == HOTRG_PREC_FP64 ? K : ((long long)K + 63) / 64 * 64;
   void *dA = nullptr, *dB = nullptr, *dC = nullptr, *pA = nullptr, *pB = nullptr, *c32 = nullptr;
   int* err = nullptr;
@@ -2127,8 +2116,8 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
       cudaMalloc(&dC, sizeof(double) * M * N) || cudaMalloc(&err, sizeof(int)))
     fail(HOTRG_ENOMEM);
   if (status == HOTRG_OK && mode != HOTRG_PREC_FP64) {
-    if (cudaMalloc(&pA, sizeof(__nv_bfloat16) * np * M * Kpad) ||
-        cudaMalloc(&pB, sizeof(__nv_bfloat16) * np * N * Kpad) || cudaMalloc(&c32, sizeof(float) * M * N))
+    if (cudaMalloc(&pA, pbytes * np * M * Kpad) || cudaMalloc(&pB, pbytes * np * N * Kpad) ||
+        cudaMalloc(&c32, sizeof(float) * M * N))
       fail(HOTRG_ENOMEM);
   }
   if (status == HOTRG_OK) {
@@ -2138,15 +2127,13 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
     if (mode == HOTRG_PREC_FP64) {
       launch_gemm_nt_f64((const double*)dA, K, (const double*)dB, K, (double*)dC, N, 0, M, N, K, 1, 0, s);
     } else {
-      cudaMemset(pA, 0, sizeof(__nv_bfloat16) * np * M * Kpad);
-      cudaMemset(pB, 0, sizeof(__nv_bfloat16) * np * N * Kpad);
-      launch_split_bf16((const double*)dA, M, K, K, (__nv_bfloat16*)pA, Kpad, M * Kpad, np, s);
-      launch_split_bf16((const double*)dB, N, K, K, (__nv_bfloat16*)pB, Kpad, N * Kpad, np, s);
-      int ta3[3] = {1, 0, 0}, tb3[3] = {0, 1, 0};
-      int ta6[6] = {2, 1, 0, 1, 0, 0}, tb6[6] = {0, 1, 2, 0, 1, 0};
-      if (launch_tc_gemm((const __nv_bfloat16*)pA, M, (const __nv_bfloat16*)pB, N, (int)Kpad, np,
-                         np == 2 ? 3 : 6, np == 2 ? ta3 : ta6, np == 2 ? tb3 : tb6, (float*)c32, N, err,
-                         s, nullptr) != 0)
+      cudaMemset(pA, 0, pbytes * np * M * Kpad);
+      cudaMemset(pB, 0, pbytes * np * N * Kpad);
+      launch_split((const double*)dA, M, K, K, pA, Kpad, M * Kpad, np, pfmt, s);
+      launch_split((const double*)dB, N, K, K, pB, Kpad, N * Kpad, np, pfmt, s);
+      int ta[6], tb[6];
+      const int nt = split_terms(np, ta, tb);
+      if (launch_tc_gemm(pA, M, pB, N, (int)Kpad, np, nt, ta, tb, (float*)c32, N, err, s, nullptr, pfmt) != 0)
         fail(HOTRG_ECUDA);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) fail(HOTRG_ECUDA);
@@ -2361,12 +2348,12 @@ int hotrg_step_times(hotrg_ctx* c, double ms[16], int launches[16], int* n, int*
 }
 
 int hotrg_gemm_rate(int mode, int M, int N, int K, int iters, double* ms_per_launch) {
-  if ((mode != HOTRG_PREC_BF16X3 && mode != HOTRG_PREC_BF16X6) || M < 1 || N < 1 || K < 1 || M > (1 << 20) ||
+  if (mode <= HOTRG_PREC_FP64 || mode > HOTRG_PREC_TF32X3 || M < 1 || N < 1 || K < 1 || M > (1 << 20) ||
       N > (1 << 20) || K > (1 << 20) || iters < 1 || !ms_per_launch)
     return HOTRG_EINVAL;
   if (!tc_gemm_ready()) return HOTRG_ECUDA;
-  const int r = measure_tc_gemm_rate(mode == HOTRG_PREC_BF16X3 ? 2 : 3, M, N, (K + 63) / 64 * 64, iters,
-                                     ms_per_launch);
+  const int r = measure_tc_gemm_rate(split_pieces(mode), M, N, (K + 63) / 64 * 64, iters, ms_per_launch,
+                                     split_format(mode));
   if (r == -1) return HOTRG_EINVAL;
   if (r == -2) return HOTRG_ENOMEM;
   if (r == -3) return HOTRG_ECUDA;

@@ -64,17 +64,86 @@ struct ChainDesc {
   long long total;     // product of size[] (< 2^32)
   unsigned magic[kMaxDims];   // q = (umulhi(x, magic) + x) >> shift == x / size, 32-bit x
   int shift[kMaxDims];
-  long long piece_stride;  // split outputs: distance between BF16 pieces
+  long long piece_stride;  // split outputs: distance between pieces (elements)
   int npieces;
+  int pfmt;                // split outputs: PIECE_BF16 or PIECE_TF32
 };
+
+// ---- operand pieces of the split forms: x = x_0 + x_1 + ..., x_0 = x rounded to the
+// piece format, x_p = the remainder after x_0 .. x_{p-1}, rounded
+enum { PIECE_BF16 = 0, PIECE_TF32 = 1 };
+inline int piece_bytes(int pfmt) { return pfmt == PIECE_TF32 ? 4 : 2; }
+// pieces per operand and their format for a split precision mode (enum hotrg_precision)
+inline int split_pieces(int mode) { return mode == 1 || mode == 4 ? 2 : (mode == 3 ? 1 : 3); }
+inline int split_format(int mode) { return mode >= 3 ? PIECE_TF32 : PIECE_BF16; }
+
+// The piece products (terms) x_a y_b of the split GEMM: every term of order 2^-(8 or
+// 11) x (a + b) up to the pieces' resolution (1 piece: 1 term; 2: 3; 3: 6).  Returns
+// the number of terms.
+inline int split_terms(int npieces, int* ta, int* tb) {
+  static const int a1[1] = {0}, b1[1] = {0};
+  static const int a2[3] = {1, 0, 0}, b2[3] = {0, 1, 0};
+  static const int a3[6] = {2, 1, 0, 1, 0, 0}, b3[6] = {0, 1, 2, 0, 1, 0};
+  const int n = npieces == 1 ? 1 : (npieces == 2 ? 3 : 6);
+  const int* a = npieces == 1 ? a1 : (npieces == 2 ? a2 : a3);
+  const int* b = npieces == 1 ? b1 : (npieces == 2 ? b2 : b3);
+  for (int t = 0; t < n; ++t) {
+    ta[t] = a[t];
+    tb[t] = b[t];
+  }
+  return n;
+}
+
+#ifdef __CUDACC__
+// x rounded to TF32 (10 stored mantissa bits, ties to even) in an FP32 word whose low
+// 13 bits are zero; infinities and NaNs pass unchanged
+__device__ __forceinline__ float round_tf32(float x) {
+  unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u += 0xfffu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xffffe000u);
+}
+
+__device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 bf16_rn(double x) { return __double2bfloat16(x); }
+
+// x as npieces pieces of format PF: piece p at element off + p * pstride of o
+template <int PF, typename T>
+__device__ __forceinline__ void store_pieces_as(void* o, long long off, long long pstride, int npieces, T x) {
+  if (PF == PIECE_TF32) {
+    float* of = (float*)o + off;
+    for (int p = 0; p < npieces; ++p) {
+      const float v = round_tf32((float)x);
+      of[p * pstride] = v;
+      x -= (T)v;
+    }
+  } else {
+    __nv_bfloat16* ob = (__nv_bfloat16*)o + off;
+    for (int p = 0; p < npieces; ++p) {
+      const __nv_bfloat16 v = bf16_rn(x);
+      ob[p * pstride] = v;
+      x -= (T)__bfloat162float(v);
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void store_pieces(void* o, long long off, long long pstride, int npieces, int pfmt,
+                                             T x) {
+  if (pfmt == PIECE_TF32)
+    store_pieces_as<PIECE_TF32>(o, off, pstride, npieces, x);
+  else
+    store_pieces_as<PIECE_BF16>(o, off, pstride, npieces, x);
+}
+#endif
 
 // ---- kernels_tensor.cu
 void launch_init_ising(double* T, int d, double beta, double h, cudaStream_t s);
 void launch_permute(const double* in, double* out, int ndim, const long long* out_size,
                     const long long* in_stride, double scale, cudaStream_t s);
-void launch_split_bf16(const double* in, long long rows, long long cols, long long ld_in,
-                       __nv_bfloat16* out, long long ld_out, long long piece_stride, int npieces,
-                       cudaStream_t s, const double* in2 = nullptr);
+// FP64 (in, + in2 when given) -> npieces pieces of format pfmt
+void launch_split(const double* in, long long rows, long long cols, long long ld_in, void* out,
+                  long long ld_out, long long piece_stride, int npieces, int pfmt, cudaStream_t s,
+                  const double* in2 = nullptr);
 void launch_trace_y(const double* Tn, int chi_c, long long pn, double* Y, cudaStream_t s);
 void launch_finish_step(double* Y, int chi_c, DevState* st, int p, int first, cudaStream_t s);
 void launch_scale(const double* in, double* out, long long n, const DevState* st, cudaStream_t s);
@@ -125,7 +194,7 @@ enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2, OUT_Z2_SPLIT = 3 };
 // positions), so the lanes of a warp hold consecutive positions of one block row.  An
 // output goes to block b = parity(k) if its row's parity p_N satisfies p_N ^ q == b
 // (the other half meets only zero blocks of T and is not formed), at row cpos[row] and
-// column = the position of k in its list; split into BF16 pieces.
+// column = the position of k in its list; split into pieces (format pfmt of the stage).
 struct Z2Out {
   const int* kcat;        // dense k of every position of the two K lists (R entries)
   unsigned R;             // entries of kcat (product of the k dims)
@@ -133,7 +202,7 @@ struct Z2Out {
   const int* cblk;        // per column (n', n~) of this sub-slice: parity p_N
   const int* cpos;        // per column: position in the list of its parity
   int q;                  // parity of the c'-slice
-  __nv_bfloat16* blk[2];  // the blocks
+  void* blk[2];           // the blocks
   long long ld[2];        // row pitch of block b (Kp_b)
   long long pstride[2];   // piece stride of block b
   long long kpad;         // row pitch of the dense out view
@@ -179,14 +248,15 @@ void launch_z2_reduce_sym(const double* p0, int ns0, int m0, const double* p1, i
 void launch_z2_reduce_sum_t(const double* p0, int ns0, int m0, const double* p1, int ns1, int m1,
                             const int* blk, const int* pos, int m, double* dS, cudaStream_t s);
 void launch_z2_gather_split(const double* src, long long ld, const int* rowmap, int nrows,
-                            const int* colmap, int ncols, __nv_bfloat16* dst, long long piece_stride,
-                            int npieces, cudaStream_t s);
+                            const int* colmap, int ncols, void* dst, long long piece_stride,
+                            int npieces, int pfmt, cudaStream_t s);
 void launch_z2_gather_f64(const double* src, long long ld, const int* rowmap, int nrows,
                           const int* colmap, int ncols, double* dst, cudaStream_t s);
-void launch_z2_gather_bf16(const __nv_bfloat16* src, long long ld, long long src_piece_stride,
-                           const int* rowmap, int nrows, const int* colmap, int ncols,
-                           __nv_bfloat16* dst, long long dst_piece_stride, int npieces,
-                           cudaStream_t s);
+// gathers pieces of either format (a copy of their bits)
+void launch_z2_gather_pieces(const void* src, long long ld, long long src_piece_stride,
+                             const int* rowmap, int nrows, const int* colmap, int ncols,
+                             void* dst, long long dst_piece_stride, int npieces, int pfmt,
+                             cudaStream_t s);
 void launch_z2_scatter_f32(const float* c0, long long ld0, const float* c1, long long ld1,
                            const int* rowblk, const int* rowpos, const int* colblk, const int* colpos,
                            int q, int nrows, int ncols, float* dense, cudaStream_t s);
@@ -196,13 +266,14 @@ void launch_z2_scatter_f64(const double* c0, long long ld0, const double* c1, lo
 
 // ---- kernels_tc_gemm.cu
 // C[M][N] (fp32, ldc) = sum_t Apiece[pa_t] (M x Kpad) . Bpiece[pb_t] (N x Kpad)^T,
-// Kpad a multiple of 32, accumulated in chunks of 32 along K
-int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
-                   int npieces, int nterms, const int* pa, const int* pb,
-                   float* C, long long ldc, int* err_flag, cudaStream_t s, float* ms_out);
+// pieces of format pfmt; Kpad a multiple of 32 (BF16) or of 32 (TF32, pair form only)
+int launch_tc_gemm(const void* A, int M, const void* B, int N, int Kpad, int npieces, int nterms,
+                   const int* pa, const int* pb, float* C, long long ldc, int* err_flag, cudaStream_t s,
+                   float* ms_out, int pfmt = PIECE_BF16);
 int tc_gemm_ready();
-// milliseconds per launch of the split-BF16 GEMM on device-resident operands (rate probe)
-int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch);
+// milliseconds per launch of the split GEMM on device-resident operands (rate probe)
+int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch,
+                         int pfmt = PIECE_BF16);
 
 // ---- kernels_tensor.cu: streaming multiprocessors of the current device (cached per device)
 int sm_count();

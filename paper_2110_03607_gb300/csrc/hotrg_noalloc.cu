@@ -94,12 +94,11 @@ extern "C" int hotrg_gemm_nt_noalloc(int mode, int M, int N, int K, const double
         status = HOTRG_ECUDA;
     }
     if (status == HOTRG_OK) {
-      launch_split_bf16(A, M, K, K, pa, Kpad, (long long)M * Kpad, np, s);
-      launch_split_bf16(B, N, K, K, pb, Kpad, (long long)N * Kpad, np, s);
-      int ta3[3] = {1, 0, 0}, tb3[3] = {0, 1, 0};
-      int ta6[6] = {2, 1, 0, 1, 0, 0}, tb6[6] = {0, 1, 2, 0, 1, 0};
-      if (launch_tc_gemm(pa, M, pb, N, (int)Kpad, np, np == 2 ? 3 : 6, np == 2 ? ta3 : ta6,
-                         np == 2 ? tb3 : tb6, c32, N, err, s, nullptr) != 0)
+      launch_split(A, M, K, K, pa, Kpad, (long long)M * Kpad, np, PIECE_BF16, s);
+      launch_split(B, N, K, K, pb, Kpad, (long long)N * Kpad, np, PIECE_BF16, s);
+      int ta[6], tb[6];
+      const int nt = split_terms(np, ta, tb);
+      if (launch_tc_gemm(pa, M, pb, N, (int)Kpad, np, nt, ta, tb, c32, N, err, s, nullptr, PIECE_BF16) != 0)
         status = HOTRG_ECUDA;
     }
     if (status == HOTRG_OK) {

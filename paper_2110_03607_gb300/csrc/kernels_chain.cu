@@ -11,9 +11,6 @@
 
 namespace hotrg {
 
-__device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
-__device__ __forceinline__ __nv_bfloat16 to_bf16(double x) { return __double2bfloat16(x); }
-
 // Row pitch of U~ in shared memory.  FP32: NN + 4 words keeps every row 16-byte
 // aligned for float4 loads (one LDS.128 per four FMAs) and puts the rows of eight
 // consecutive hat indices (lanes of the prime side) on distinct bank groups.  FP64:
@@ -168,16 +165,18 @@ __global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) 
       for (int n = 0; n < NN; ++n)
         if (n < d.nn) o[out_off + n * d.n_out_stride] = (double)acc[n];
     } else if (OUT == OUT_BF16_SPLIT) {
-      __nv_bfloat16* o = (__nv_bfloat16*)out;
+      // the format branch outside the unrolled loop keeps one copy of it live
+      if (d.pfmt == PIECE_TF32) {
 #pragma unroll
-      for (int n = 0; n < NN; ++n) {
-        if (n >= d.nn) break;
-        TAcc x = acc[n];
-        long long off = out_off + n * d.n_out_stride;
-        for (int p = 0; p < d.npieces; ++p) {
-          __nv_bfloat16 bv = to_bf16(x);
-          o[off + p * d.piece_stride] = bv;
-          x -= (TAcc)__bfloat162float(bv);
+        for (int n = 0; n < NN; ++n) {
+          if (n >= d.nn) break;
+          store_pieces_as<PIECE_TF32>(out, out_off + n * d.n_out_stride, d.piece_stride, d.npieces, acc[n]);
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+          if (n >= d.nn) break;
+          store_pieces_as<PIECE_BF16>(out, out_off + n * d.n_out_stride, d.piece_stride, d.npieces, acc[n]);
         }
       }
     } else {
@@ -187,19 +186,23 @@ __global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) 
       const int kb = kidx >= zo.rb0 ? 1 : 0;
       const long long kpos = (long long)(kb ? kidx - zo.rb0 : kidx);
       // selects, not an index: an indexed parameter array would be copied to local memory
-      __nv_bfloat16* ob = (kb ? zo.blk[1] : zo.blk[0]) + kpos;
+      void* ob = kb ? zo.blk[1] : zo.blk[0];
       const long long ld = kb ? zo.ld[1] : zo.ld[0], ps = kb ? zo.pstride[1] : zo.pstride[0];
+      if (d.pfmt == PIECE_TF32) {
 #pragma unroll
-      for (int n = 0; n < NN; ++n) {
-        if (n >= d.nn) break;
-        const long long row = row0 + n * zo.nrow_step;
-        if ((zo.cblk[row] ^ zo.q) != kb) continue;
-        __nv_bfloat16* o = ob + (long long)zo.cpos[row] * ld;
-        TAcc x = acc[n];
-        for (int p = 0; p < d.npieces; ++p) {
-          __nv_bfloat16 bv = to_bf16(x);
-          o[p * ps] = bv;
-          x -= (TAcc)__bfloat162float(bv);
+        for (int n = 0; n < NN; ++n) {
+          if (n >= d.nn) break;
+          const long long row = row0 + n * zo.nrow_step;
+          if ((zo.cblk[row] ^ zo.q) != kb) continue;
+          store_pieces_as<PIECE_TF32>(ob, kpos + (long long)zo.cpos[row] * ld, ps, d.npieces, acc[n]);
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+          if (n >= d.nn) break;
+          const long long row = row0 + n * zo.nrow_step;
+          if ((zo.cblk[row] ^ zo.q) != kb) continue;
+          store_pieces_as<PIECE_BF16>(ob, kpos + (long long)zo.cpos[row] * ld, ps, d.npieces, acc[n]);
         }
       }
     }

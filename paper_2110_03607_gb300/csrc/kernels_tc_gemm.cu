@@ -1,7 +1,8 @@
 // Bottleneck contraction (Sec. 4.2.9, Eq. BottleneckPart) on the 5th-generation
 // tensor cores:
 //   C[(c, n^), (n', n~)] = sum_{(rho, n^')} T[(c, n^), (rho, n^')] B[(n', n~), (rho, n^')]
-// with both operands split into BF16 pieces, x = x_0 + x_1 (+ x_2), and the
+// with both operands split into BF16 pieces, x = x_0 + x_1 (+ x_2), or into TF32
+// pieces (FP32 words whose low 13 mantissa bits are zero), x = x_0 (+ x_1), and the
 // product formed as a sum of piece products (terms) x_i y_j.
 //
 // Two persistent kernels; launch_tc_gemm uses the CTA-pair one (HOTRG_TC_USE_PAIR).
@@ -10,8 +11,11 @@
 // 256 x 256 tile of C; CTA 0 issues tcgen05.mma with M = 256, N = 256, K = 16.  CTA r
 // holds rows 128 r .. of the A tile and rows 128 r .. of the B tile, so each SM
 // receives only half of the B tile: the per-SM copy rate, not the tensor pipe or the
-// L2, is what bounds the one-CTA form below.  K slabs of 64 BF16 (128-byte rows,
-// 128-byte swizzle), every piece of a slab in one of two 96 KiB ring stages.
+// L2, is what bounds the one-CTA form below.  K slabs of 128-byte rows (64 BF16 or 32
+// TF32, 128-byte swizzle), every piece of a slab in one ring stage (6 / npieces stages
+// of npieces x 32 KiB);
+// kind::f16 MMAs take K = 16 BF16, kind::tf32 MMAs K = 8 TF32: 32 bytes of a row
+// either way.  The TF32 pieces run only in this form.
 //
 // tc_gemm_kernel (cta_group::1): one CTA per SM walks 128 x 256 tiles; K slabs of 32
 // BF16 (64-byte rows) in a 3-stage ring, every piece of a slab in one stage.
@@ -171,6 +175,12 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N, M.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32 (format 2), both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
 }
 
@@ -449,8 +459,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // CTA-pair form (cta_group::2): a cluster of two CTAs on two SMs computes a 256 x 256
 // tile of C with M = 256 MMAs issued by CTA 0.  CTA r holds rows 128 r .. of the A
 // tile and rows 128 r .. of the B tile (N) in its own shared memory, so each SM
-// receives half of B; K slabs of 64 BF16 (128-byte rows, 128-byte swizzle), every
-// piece of a slab in one of two ring stages (96 KiB each).  CTA r's TMEM holds rows
+// receives half of B; K slabs of 128-byte rows (128-byte swizzle), every piece of a
+// slab in one ring stage.  The ring holds six 32 KiB units (one piece of A and one of
+// B): 6 / npieces stages, so forms with fewer pieces keep more slabs in flight.
+// CTA r's TMEM holds rows
 // 128 r .. of the accumulator.  CTA 1's copies complete on its own barrier; a thread
 // of CTA 1 then arrives on CTA 0's barrier, whose MMA thread waits for both.  The
 // MMA completions arrive on the ring and accumulator barriers of both CTAs.
@@ -459,11 +471,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #define HOTRG_TC_USE_PAIR 1
 #endif
 namespace {
-constexpr int P_TK = 64, P_STAGES = 2;
+constexpr int P_TK = 64, P_UNITS = 6, P_MAXST = 6;
 constexpr int P_A_PIECE = 128 * P_TK * 2;                    // 16 KiB: this CTA's A rows
 constexpr int P_B_PIECE = 128 * P_TK * 2;                    // 16 KiB: this CTA's B rows
-constexpr int P_STAGE = MAXP * (P_A_PIECE + P_B_PIECE);      // 96 KiB
-constexpr int P_SMEM = 1024 + P_STAGES * P_STAGE + 256;
+constexpr int P_UNIT = P_A_PIECE + P_B_PIECE;                // one piece of each operand
+constexpr int P_SMEM = 1024 + P_UNITS * P_UNIT + 256;
 constexpr int P_NTHREADS = 320;                              // 8 epilogue warps + producer + MMA/relay
 static_assert(P_SMEM <= 227 * 1024, "shared memory of one CTA");
 }  // namespace
@@ -495,14 +507,23 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                               uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <bool TF32>
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  if (TF32)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 // arrives on the mbarrier at bar's offset in every CTA of cta_mask once the pair MMAs
@@ -515,6 +536,7 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t cta_mas
       : "memory");
 }
 
+template <bool TF32>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         float* __restrict__ C, int M, int N, long long ldc, int kslabs, TcTerms terms,
@@ -522,9 +544,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   volatile int* gerr = g_err;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + P_STAGES * P_STAGE);
-  uint64_t* empty = full + P_STAGES;
-  uint64_t* tfull = empty + P_STAGES;    // [2] MMA -> epilogue (both CTAs)
+  uint64_t* full = (uint64_t*)(smem + P_UNITS * P_UNIT);
+  uint64_t* empty = full + P_MAXST;
+  uint64_t* tfull = empty + P_MAXST;     // [2] MMA -> epilogue (both CTAs)
   uint64_t* tempty = tfull + 2;          // [2] epilogue of both CTAs -> MMA (CTA 0)
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -539,9 +561,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
   const long long tiles_here = ngroups > cid ? (ngroups - 1 - cid) / ncl + 1 : 0;
   auto grp = [&](long long i) { return cid + i * ncl; };
   const int np = terms.npieces;
+  const int nst = P_UNITS / np;                 // ring stages
+  const int stage_bytes = np * P_UNIT;          // A pieces, then B pieces
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < P_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(full + s, leader ? 2 : 1);   // CTA 0: its own copies and CTA 1's relay
       mbar_init(empty + s, 1);
     }
@@ -576,8 +600,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
       long long issued = 0;
       bool ok = true;
       for (long long g = 0; g < total; ++g) {
-        const int s = (int)(g % P_STAGES);
-        const uint32_t ph = (uint32_t)(g / P_STAGES) & 1u;
+        const int s = (int)(g % nst);
+        const uint32_t ph = (uint32_t)(g / nst) & 1u;
         if (!mbar_wait(empty + s, ph ^ 1u, cta_abort, gerr)) {
           ok = false;
           break;
@@ -586,16 +610,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
         const int kb = (int)(g % kslabs);
         const int m0 = (int)(gg % mgroups) * 256 + (int)rank * 128;
         const int nb0 = (int)(gg / mgroups) * 256 + (int)rank * 128;
-        uint8_t* st = smem + s * P_STAGE;
-        mbar_expect_tx(full + s, (uint32_t)(np * (P_A_PIECE + P_B_PIECE)));
-        for (int p = 0; p < np; ++p) tma_load_3d(&tmA, st + p * P_A_PIECE, full + s, kb * P_TK, m0, p);
+        const int k0 = kb * (TF32 ? P_TK / 2 : P_TK);   // elements of a 128-byte row
+        uint8_t* st = smem + s * stage_bytes;
+        mbar_expect_tx(full + s, (uint32_t)stage_bytes);
+        for (int p = 0; p < np; ++p) tma_load_3d(&tmA, st + p * P_A_PIECE, full + s, k0, m0, p);
         for (int p = 0; p < np; ++p)
-          tma_load_3d(&tmB, st + MAXP * P_A_PIECE + p * P_B_PIECE, full + s, kb * P_TK, nb0, p);
+          tma_load_3d(&tmB, st + np * P_A_PIECE + p * P_B_PIECE, full + s, k0, nb0, p);
         issued = g + 1;
       }
-      for (long long g = issued > P_STAGES ? issued - P_STAGES : 0; g < issued; ++g) {
-        const int s = (int)(g % P_STAGES);
-        const uint32_t ph = (uint32_t)(g / P_STAGES) & 1u;
+      for (long long g = issued > nst ? issued - nst : 0; g < issued; ++g) {
+        const int s = (int)(g % nst);
+        const uint32_t ph = (uint32_t)(g / nst) & 1u;
         unsigned long long t0 = gtimer();
         if (ok && !mbar_wait(empty + s, ph, cta_abort, gerr)) ok = false;
         if (!ok)
@@ -608,35 +633,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
     if (lane == 0 && !leader) {
       // ---------------- relay (CTA 1): each slab of this CTA has landed -> CTA 0
       for (long long g = 0; g < total; ++g) {
-        const int s = (int)(g % P_STAGES);
-        if (!mbar_wait(full + s, (uint32_t)(g / P_STAGES) & 1u, cta_abort, gerr)) break;
+        const int s = (int)(g % nst);
+        if (!mbar_wait(full + s, (uint32_t)(g / nst) & 1u, cta_abort, gerr)) break;
         mbar_arrive_rank(full + s, 0);
       }
     } else if (lane == 0) {
-      // ---------------- MMA issuer (CTA 0): M = 256, N = 256, K = 16; one chunk per slab,
-      // its small terms first
-      constexpr uint32_t idesc = idesc_bf16_f32(256, 256);
+      // ---------------- MMA issuer (CTA 0): M = 256, N = 256, K = 32 bytes of a row;
+      // one chunk per slab, its small terms first
+      constexpr uint32_t idesc = TF32 ? idesc_tf32_f32(256, 256) : idesc_bf16_f32(256, 256);
       bool ok = true;
       for (long long g = 0; g < total && ok; ++g) {
         const int b = (int)(g & 1);
         if (g >= 2 && !mbar_wait(tempty + b, (uint32_t)((g >> 1) - 1) & 1u, cta_abort, gerr)) break;
         tc_fence_after();
-        const int s = (int)(g % P_STAGES);
-        if (!mbar_wait(full + s, (uint32_t)(g / P_STAGES) & 1u, cta_abort, gerr)) {
+        const int s = (int)(g % nst);
+        if (!mbar_wait(full + s, (uint32_t)(g / nst) & 1u, cta_abort, gerr)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t dst = tmem + (uint32_t)(b * 256);
-        const uint32_t st = su32(smem + s * P_STAGE);
+        const uint32_t st = su32(smem + s * stage_bytes);
         for (int t = 0; t < terms.nterms; ++t) {
           const int pa_t = (int)(terms.code >> (4 * t)) & 3, pb_t = (int)(terms.code >> (4 * t + 2)) & 3;
           const uint64_t a0 = sdesc_sw128(st + pa_t * P_A_PIECE);
-          const uint64_t b0 = sdesc_sw128(st + MAXP * P_A_PIECE + pb_t * P_B_PIECE);
+          const uint64_t b0 = sdesc_sw128(st + np * P_A_PIECE + pb_t * P_B_PIECE);
 #pragma unroll
-          for (int kk = 0; kk < P_TK / 16; ++kk)
-            umma_bf16_pair(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
-                           (t != 0 || kk != 0) ? 1u : 0u);
+          for (int kk = 0; kk < P_TK / 16; ++kk)   // 32 bytes (2 descriptor units) per MMA
+            umma_pair<TF32>(dst, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
+                            (t != 0 || kk != 0) ? 1u : 0u);
         }
         umma_commit_pair(empty + s, (uint16_t)0x3);   // the slot of both CTAs is free
         umma_commit_pair(tfull + b, (uint16_t)0x3);   // the chunk is in both CTAs' TMEM
@@ -735,18 +760,21 @@ static EncodeTiledFn get_encode() {
 
 int tc_gemm_ready() { return get_encode() != nullptr; }
 
-// operand pieces stored as [piece][rows][kpad] BF16; one box = TK columns of K
-// (SW_BYTES, the swizzle width) x box_rows rows of one piece
-static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kpad, int npieces,
-                    int box_rows, int box_k = TK) {
+// operand pieces stored as [piece][rows][kpad] elements (BF16, or TF32 in FP32 words);
+// one box = box_k elements of K (box_k x element size = the swizzle width) x box_rows
+// rows of one piece
+static int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int npieces, int box_rows,
+                    int box_k = TK, bool tf32 = false) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return -1;
+  const cuuint64_t esz = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)npieces};
-  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
+  cuuint64_t strides[2] = {(cuuint64_t)kpad * esz, (cuuint64_t)kpad * esz * (cuuint64_t)rows};
   cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base,
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   box_k * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     fprintf(stderr, "hotrg: tensor map encoding failed (CUresult %d; rows %d, kpad %d)\n", (int)r, rows,
@@ -774,20 +802,25 @@ static bool pair_smem_attr_set() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return true;
-  if (cudaFuncSetAttribute(tc_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(tc_gemm_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(tc_gemm_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM) !=
+          cudaSuccess)
     return false;
   if (dev >= 0 && dev < kMaxDevices) done[dev].store(1, std::memory_order_release);
   return true;
 }
 
-int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int Kpad,
-                   int npieces, int nterms, const int* pa, const int* pb, float* C, long long ldc,
-                   int* err_flag, cudaStream_t s, float* ms_out) {
-  if (Kpad % TK != 0 || Kpad < TK || nterms < 1 || nterms > 9 || npieces < 1 || npieces > MAXP || M < 1 ||
-      N < 1 || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
-    fprintf(stderr, "hotrg: GEMM arguments rejected (M %d, N %d, Kpad %d, pieces %d, terms %d, A %p, B %p)\n",
-            M, N, Kpad, npieces, nterms, (const void*)A, (const void*)B);
+int launch_tc_gemm(const void* A, int M, const void* B, int N, int Kpad, int npieces, int nterms,
+                   const int* pa, const int* pb, float* C, long long ldc, int* err_flag, cudaStream_t s,
+                   float* ms_out, int pfmt) {
+  const bool tf32 = pfmt == PIECE_TF32;
+  // TF32 pieces: 32-element (128-byte) slabs in the pair form only
+  if (Kpad % (tf32 ? P_TK / 2 : TK) != 0 || Kpad < TK || nterms < 1 || nterms > 9 || npieces < 1 ||
+      npieces > MAXP || M < 1 || N < 1 || (pfmt != PIECE_BF16 && !tf32) || (tf32 && !HOTRG_TC_USE_PAIR) ||
+      (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) {
+    fprintf(stderr, "hotrg: GEMM arguments rejected (M %d, N %d, Kpad %d, pieces %d, terms %d, format %d, A %p, B %p)\n",
+            M, N, Kpad, npieces, nterms, pfmt, A, B);
     return -1;
   }
   {
@@ -797,10 +830,12 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
       return -1;
     }
   }
-  const bool use_pair = HOTRG_TC_USE_PAIR != 0 && Kpad % P_TK == 0;
+  const bool use_pair = tf32 || (HOTRG_TC_USE_PAIR != 0 && Kpad % P_TK == 0);
+  const int slab_k = tf32 ? P_TK / 2 : P_TK;   // elements of a 128-byte row
   CUtensorMap ma, mb;
   if (use_pair) {
-    if (make_map(&ma, A, M, Kpad, npieces, 128, P_TK) || make_map(&mb, B, N, Kpad, npieces, 128, P_TK)) return -1;
+    if (make_map(&ma, A, M, Kpad, npieces, 128, slab_k, tf32) || make_map(&mb, B, N, Kpad, npieces, 128, slab_k, tf32))
+      return -1;
   } else if (make_map(&ma, A, M, Kpad, npieces, TM) || make_map(&mb, B, N, Kpad, npieces, TN)) {
     return -1;
   }
@@ -838,8 +873,10 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  if (use_pair)
-    tc_gemm_pair_kernel<<<grid, P_NTHREADS, P_SMEM, s>>>(ma, mb, C, M, N, ldc, Kpad / P_TK, terms, err_flag);
+  if (use_pair && tf32)
+    tc_gemm_pair_kernel<true><<<grid, P_NTHREADS, P_SMEM, s>>>(ma, mb, C, M, N, ldc, Kpad / slab_k, terms, err_flag);
+  else if (use_pair)
+    tc_gemm_pair_kernel<false><<<grid, P_NTHREADS, P_SMEM, s>>>(ma, mb, C, M, N, ldc, Kpad / slab_k, terms, err_flag);
   else
     tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, C, M, N, ldc, Kpad / TK, terms, err_flag);
   ++g_launches;
@@ -858,25 +895,34 @@ int launch_tc_gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N,
   return 0;
 }
 
-// Operand pieces for the rate probe: small integers (exact in BF16) from a hash
-__global__ void fill_pieces_kernel(__nv_bfloat16* p, long long n, unsigned seed) {
+// Operand pieces for the rate probe: small multiples of 1/8 (exact in BF16 and in
+// TF32) from a hash
+__global__ void fill_pieces_kernel(void* p, long long n, unsigned seed, int tf32) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     unsigned x = (unsigned)i * 2654435761u ^ seed;
     x ^= x >> 15;
     x *= 2246822519u;
     x ^= x >> 13;
-    p[i] = __float2bfloat16((float)((int)(x % 17u) - 8) * 0.125f);
+    const float v = (float)((int)(x % 17u) - 8) * 0.125f;
+    if (tf32)
+      ((float*)p)[i] = v;
+    else
+      ((__nv_bfloat16*)p)[i] = __float2bfloat16(v);
   }
 }
 
-int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch) {
-  if (npieces < 2 || npieces > MAXP || M < 1 || N < 1 || Kpad < TK || Kpad % TK || iters < 1) return -1;
-  __nv_bfloat16 *A = nullptr, *B = nullptr;
+int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double* ms_per_launch, int pfmt) {
+  const bool tf32 = pfmt == PIECE_TF32;
+  if (npieces < (tf32 ? 1 : 2) || npieces > (tf32 ? 2 : MAXP) || M < 1 || N < 1 || Kpad < TK || Kpad % TK ||
+      iters < 1)
+    return -1;
+  void *A = nullptr, *B = nullptr;
   float* C = nullptr;
   int* err = nullptr;
+  const long long esz = tf32 ? 4 : 2;
   const long long na = (long long)npieces * M * Kpad, nb = (long long)npieces * N * Kpad;
-  if (cudaMalloc(&A, 2 * na) != cudaSuccess || cudaMalloc(&B, 2 * nb) != cudaSuccess ||
+  if (cudaMalloc(&A, esz * na) != cudaSuccess || cudaMalloc(&B, esz * nb) != cudaSuccess ||
       cudaMalloc(&C, 4LL * M * N) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(A);
@@ -886,21 +932,18 @@ int measure_tc_gemm_rate(int npieces, int M, int N, int Kpad, int iters, double*
     return -2;
   }
   cudaMemset(err, 0, sizeof(int));
-  fill_pieces_kernel<<<4 * sm_count(), 256>>>(A, na, 1u);
-  fill_pieces_kernel<<<4 * sm_count(), 256>>>(B, nb, 2u);
+  fill_pieces_kernel<<<4 * sm_count(), 256>>>(A, na, 1u, tf32 ? 1 : 0);
+  fill_pieces_kernel<<<4 * sm_count(), 256>>>(B, nb, 2u, tf32 ? 1 : 0);
   g_launches += 2;
-  int ta3[3] = {1, 0, 0}, tb3[3] = {0, 1, 0};
-  int ta6[6] = {2, 1, 0, 1, 0, 0}, tb6[6] = {0, 1, 2, 0, 1, 0};
-  const int nt = npieces == 2 ? 3 : 6;
-  int r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, npieces == 2 ? ta3 : ta6, npieces == 2 ? tb3 : tb6,
-                         C, N, err, 0, nullptr);   // warm-up
+  int ta[6], tb[6];
+  const int nt = split_terms(npieces, ta, tb);
+  int r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, ta, tb, C, N, err, 0, nullptr, pfmt);   // warm-up
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, 0);
   for (int i = 0; i < iters && r == 0; ++i)
-    r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, npieces == 2 ? ta3 : ta6, npieces == 2 ? tb3 : tb6, C,
-                       N, err, 0, nullptr);
+    r = launch_tc_gemm(A, M, B, N, Kpad, npieces, nt, ta, tb, C, N, err, 0, nullptr, pfmt);
   cudaEventRecord(e1, 0);
   cudaEventSynchronize(e1);
   float ms = 0.0f;

@@ -101,34 +101,29 @@ void launch_permute(const double* in, double* out, int ndim, const long long* ou
   ++g_launches;
 }
 
-// FP64 -> npieces BF16 pieces: p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1),
+// FP64 -> npieces pieces (BF16 or TF32): p0 = rnd(x), p1 = rnd(x - p0), p2 = rnd(x - p0 - p1),
 // with x = in (+ in2, the same layout, when given).
-__global__ void split_bf16_kernel(const double* __restrict__ in, const double* __restrict__ in2, long long rows,
-                                  long long cols, long long ld_in, __nv_bfloat16* __restrict__ out,
-                                  long long ld_out, long long piece_stride, int npieces) {
+__global__ void split_kernel(const double* __restrict__ in, const double* __restrict__ in2, long long rows,
+                             long long cols, long long ld_in, void* __restrict__ out, long long ld_out,
+                             long long piece_stride, int npieces, int pfmt) {
   long long total = rows * cols;
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
     long long r = e / cols, c = e - r * cols;
     double x = in2 ? in[r * ld_in + c] + in2[r * ld_in + c] : in[r * ld_in + c];
-    long long o = r * ld_out + c;
-    for (int p = 0; p < npieces; ++p) {
-      __nv_bfloat16 b = __double2bfloat16(x);
-      out[o + p * piece_stride] = b;
-      x -= (double)__bfloat162float(b);
-    }
+    store_pieces(out, r * ld_out + c, piece_stride, npieces, pfmt, x);
   }
 }
 
-void launch_split_bf16(const double* in, long long rows, long long cols, long long ld_in,
-                       __nv_bfloat16* out, long long ld_out, long long piece_stride, int npieces,
-                       cudaStream_t s, const double* in2) {
+void launch_split(const double* in, long long rows, long long cols, long long ld_in, void* out,
+                  long long ld_out, long long piece_stride, int npieces, int pfmt, cudaStream_t s,
+                  const double* in2) {
   long long total = rows * cols;
   long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > 32LL * sm_count()) blocks = 32LL * sm_count();
   if (blocks < 1) blocks = 1;
-  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, in2, rows, cols, ld_in, out, ld_out,
-                                                     piece_stride, npieces);
+  split_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, in2, rows, cols, ld_in, out, ld_out, piece_stride, npieces,
+                                                pfmt);
   ++g_launches;
 }
 

@@ -17,19 +17,15 @@ namespace hotrg {
 __global__ void z2_gather_split_kernel(const double* __restrict__ src, long long ld,
                                        const int* __restrict__ rowmap, int nrows,
                                        const int* __restrict__ colmap, int ncols,
-                                       __nv_bfloat16* __restrict__ dst, long long piece_stride,
-                                       int npieces) {
+                                       void* __restrict__ dst, long long piece_stride,
+                                       int npieces, int pfmt) {
   long long total = (long long)nrows * ncols;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e / ncols), j = (int)(e - (long long)i * ncols);
     int cj = colmap[j];
     double x = cj >= 0 ? src[(long long)rowmap[i] * ld + cj] : 0.0;
-    for (int p = 0; p < npieces; ++p) {
-      __nv_bfloat16 b = __double2bfloat16(x);
-      dst[p * piece_stride + e] = b;
-      x -= (double)__bfloat162float(b);
-    }
+    store_pieces(dst, e, piece_stride, npieces, pfmt, x);
   }
 }
 
@@ -47,28 +43,28 @@ __global__ void z2_gather_f64_kernel(const double* __restrict__ src, long long l
   }
 }
 
-// BF16 pieces: dst[p][i][j] = src[p][rowmap[i]][colmap[j]] (0 where colmap[j] < 0).
-// Rows over grid y, four consecutive columns per thread (ncols is a multiple of 4):
-// one 8-byte store per piece.
-__global__ void z2_gather_bf16_kernel(const __nv_bfloat16* __restrict__ src, long long ld,
-                                      long long src_piece_stride, const int* __restrict__ rowmap,
-                                      int nrows, const int* __restrict__ colmap, int ncols,
-                                      __nv_bfloat16* __restrict__ dst, long long dst_piece_stride,
-                                      int npieces) {
+// Pieces (E = the bits of one BF16 or TF32 element): dst[p][i][j] = src[p][rowmap[i]][colmap[j]]
+// (0 where colmap[j] < 0).  Rows over grid y, four consecutive columns per thread (ncols
+// is a multiple of 4): one 4-element store per piece.
+template <typename E, typename E4>
+__global__ void z2_gather_pieces_kernel(const E* __restrict__ src, long long ld, long long src_piece_stride,
+                                        const int* __restrict__ rowmap, int nrows,
+                                        const int* __restrict__ colmap, int ncols, E* __restrict__ dst,
+                                        long long dst_piece_stride, int npieces) {
   const int nq = ncols >> 2;
   for (int i = blockIdx.y; i < nrows; i += gridDim.y) {
-    const __nv_bfloat16* sr = src + (long long)rowmap[i] * ld;
-    __nv_bfloat16* dr = dst + (long long)i * ncols;
+    const E* sr = src + (long long)rowmap[i] * ld;
+    E* dr = dst + (long long)i * ncols;
     for (int jq = blockIdx.x * blockDim.x + threadIdx.x; jq < nq; jq += gridDim.x * blockDim.x) {
       const int4 cm = reinterpret_cast<const int4*>(colmap)[jq];
       for (int p = 0; p < npieces; ++p) {
-        const __nv_bfloat16* sp = sr + p * src_piece_stride;
-        __align__(8) __nv_bfloat16 v[4];
-        v[0] = cm.x >= 0 ? sp[cm.x] : __float2bfloat16(0.0f);
-        v[1] = cm.y >= 0 ? sp[cm.y] : __float2bfloat16(0.0f);
-        v[2] = cm.z >= 0 ? sp[cm.z] : __float2bfloat16(0.0f);
-        v[3] = cm.w >= 0 ? sp[cm.w] : __float2bfloat16(0.0f);
-        *reinterpret_cast<uint2*>(dr + p * dst_piece_stride + 4 * jq) = *reinterpret_cast<const uint2*>(v);
+        const E* sp = sr + p * src_piece_stride;
+        E4 v;
+        v.x = cm.x >= 0 ? sp[cm.x] : E(0);
+        v.y = cm.y >= 0 ? sp[cm.y] : E(0);
+        v.z = cm.z >= 0 ? sp[cm.z] : E(0);
+        v.w = cm.w >= 0 ? sp[cm.w] : E(0);
+        *reinterpret_cast<E4*>(dr + p * dst_piece_stride + 4 * jq) = v;
       }
     }
   }
@@ -129,10 +125,10 @@ static unsigned grid_for(long long total) {
 }
 
 void launch_z2_gather_split(const double* src, long long ld, const int* rowmap, int nrows,
-                            const int* colmap, int ncols, __nv_bfloat16* dst, long long piece_stride,
-                            int npieces, cudaStream_t s) {
+                            const int* colmap, int ncols, void* dst, long long piece_stride,
+                            int npieces, int pfmt, cudaStream_t s) {
   z2_gather_split_kernel<<<grid_for((long long)nrows * ncols), 256, 0, s>>>(
-      src, ld, rowmap, nrows, colmap, ncols, dst, piece_stride, npieces);
+      src, ld, rowmap, nrows, colmap, ncols, dst, piece_stride, npieces, pfmt);
   ++g_launches;
 }
 
@@ -155,12 +151,18 @@ static dim3 grid_rows(int nrows, long long units_per_row) {
   return dim3((unsigned)bx, (unsigned)by);
 }
 
-void launch_z2_gather_bf16(const __nv_bfloat16* src, long long ld, long long src_piece_stride,
-                           const int* rowmap, int nrows, const int* colmap, int ncols,
-                           __nv_bfloat16* dst, long long dst_piece_stride, int npieces,
-                           cudaStream_t s) {
-  z2_gather_bf16_kernel<<<grid_rows(nrows, ncols / 4), 256, 0, s>>>(
-      src, ld, src_piece_stride, rowmap, nrows, colmap, ncols, dst, dst_piece_stride, npieces);
+void launch_z2_gather_pieces(const void* src, long long ld, long long src_piece_stride,
+                             const int* rowmap, int nrows, const int* colmap, int ncols,
+                             void* dst, long long dst_piece_stride, int npieces, int pfmt,
+                             cudaStream_t s) {
+  if (pfmt == PIECE_TF32)
+    z2_gather_pieces_kernel<unsigned, uint4><<<grid_rows(nrows, ncols / 4), 256, 0, s>>>(
+        (const unsigned*)src, ld, src_piece_stride, rowmap, nrows, colmap, ncols, (unsigned*)dst,
+        dst_piece_stride, npieces);
+  else
+    z2_gather_pieces_kernel<unsigned short, ushort4><<<grid_rows(nrows, ncols / 4), 256, 0, s>>>(
+        (const unsigned short*)src, ld, src_piece_stride, rowmap, nrows, colmap, ncols, (unsigned short*)dst,
+        dst_piece_stride, npieces);
   ++g_launches;
 }
 

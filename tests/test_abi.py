@@ -57,3 +57,14 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setenv("HOTRG_LIBRARY", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         b.load()
+
+
+def test_binding_precision_constants_match_the_header():
+    from paper_2110_03607_gb300 import binding
+
+    src = open(os.path.join(ROOT, "include", "hotrg.h")).read()
+    body = re.search(r"enum hotrg_precision \{(.*?)\};", src, flags=re.S).group(1)
+    enum = {k: int(v) for k, v in re.findall(r"HOTRG_(PREC_[A-Z0-9]+)\s*=\s*(\d+)", body)}
+    assert set(enum) == {"PREC_FP64", "PREC_BF16X3", "PREC_BF16X6", "PREC_TF32", "PREC_TF32X3"}
+    for k, v in enum.items():
+        assert getattr(binding, k) == v, k
