@@ -366,8 +366,25 @@ def batch_arm(args):
     axes = [(FIRST_AXIS + s) % D for s in range(total)]
     for a in axes[: GROWTH_STEPS + args.warmup]:
         pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
-    torch.cuda.synchronize()
     timed = axes[GROWTH_STEPS + args.warmup:]
+    graphs = None
+    if args.graphs:
+        # captured cycles: dense steps (parities dropped: no read-back), one uncaptured
+        # cycle to place the buffers, then each instance's next 6-step cycle (lcm(2, 3))
+        # recorded once; the timed region replays whole cycles
+        cyc = 6
+        for c in ctxs:
+            pkg.hotrg_set_parity(c, None)
+        ncyc = max(1, -(-len(timed) // cyc))
+        ax_all = [(FIRST_AXIS + s) % D for s in range(GROWTH_STEPS + args.warmup + cyc * (ncyc + 1))]
+        warm_cyc = ax_all[GROWTH_STEPS + args.warmup: GROWTH_STEPS + args.warmup + cyc]
+        for a in warm_cyc:
+            pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
+        cyc_axes = ax_all[GROWTH_STEPS + args.warmup + cyc: GROWTH_STEPS + args.warmup + 2 * cyc]
+        graphs = [pkg.hotrg_graph_capture(c, cyc_axes, chi) for c, chi in zip(ctxs, chis)]
+        timed = cyc_axes * ncyc
+        axes = ax_all[: GROWTH_STEPS + args.warmup + cyc] + timed
+    torch.cuda.synchronize()
     launches0 = pkg.hotrg_launch_count(ctxs[0])
     sampler = ClockSampler(local)
     sampler.start()
@@ -377,10 +394,18 @@ def batch_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for a in timed:
-        pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
+    if graphs is not None:
+        for _ in range(len(timed) // 6):
+            for c, gr in zip(ctxs, graphs):
+                pkg.hotrg_graph_launch(c, gr)
+    else:
+        for a in timed:
+            pkg.hotrg_step_batch(ctxs, [a] * n, chis, nthreads)
     torch.cuda.synchronize()
     elapsed_ms = (time.perf_counter() - t0) * 1000.0
+    if graphs is not None:
+        for gr in graphs:
+            pkg.hotrg_graph_free(gr)
     if dist:
         dist.barrier()
     sampler.stop()
@@ -447,8 +472,10 @@ def batch_arm(args):
             "data": "synthetic (Ising initial tensors from beta, h; no dataset)",
             "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
                                    f"{args.warmup} warm-up steps, {K} timed batch steps",
-                       "precision": args.precision, "z2_blocks": args.z2 == "on",
-                       "host_workers": nthreads if nthreads > 0 else "hardware threads",
+                       "precision": args.precision,
+                       "z2_blocks": args.z2 == "on" and not args.graphs,
+                       "captured_graphs": "one 6-step cycle per instance, replayed" if args.graphs else None,
+                       "host_workers": (1 if args.graphs else (nthreads if nthreads > 0 else "hardware threads")),
                        "l2": "not flushed: the 64 instances' tensors and operands (several GB) "
                              "exceed L2 together",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -722,6 +749,9 @@ def main():
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the two timed steps of the plain FP64 form")
     ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
+    ap.add_argument("--graphs", action="store_true",
+                    help="batching workloads: replay captured 6-step cycles (dense steps) instead of "
+                         "stepping through hotrg_step_batch")
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host workers of the batching form (batch3d_mixed)")
     ap.add_argument("--z2", default="on", choices=["on", "off"],

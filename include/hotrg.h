@@ -142,7 +142,9 @@ int hotrg_set_z2(hotrg_ctx* ctx, int enable);
  * `parity` holds chis[0] entries for axis 0, then chis[1] for axis 1, ...
  * (the two legs of an axis share them).  Checked on the device: if an
  * element of odd total parity is nonzero the call returns EINVAL and the
- * parities stay unknown.  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
+ * parities stay unknown.  Synchronous.  parity = NULL forgets the parities:
+ * later steps are dense and read nothing back (so they can be captured,
+ * hotrg_graph_capture).  Errors: EINVAL, ENOMEM, ECUDA, ESTATE. */
 int hotrg_set_parity(hotrg_ctx* ctx, const int* parity);
 
 /* Read the known leg parities back in the layout of hotrg_set_parity;
@@ -194,6 +196,29 @@ int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
  * hotrg_step. */
 int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
                      int* status);
+
+/* Captured steps (CUDA graph; the paper has no counterpart).  hotrg_graph_capture
+ * records the n steps hotrg_step(ctx, axes[i], chi) would enqueue, without running
+ * them, into one executable graph.  The sequence must be closed: after it the bond
+ * dimensions, the slot order and the buffers of the tensor are those before it
+ * (the tensor alternates between two buffers every step and the slot order turns
+ * with the axis, so in steady state a closed sequence is lcm(2, d) steps of the
+ * cyclic axes: 2 in 2D, 6 in 3D, 4 in 4D); else HOTRG_ESTATE and nothing is kept.
+ * The context must be past bond growth and must have run the same steps once
+ * uncaptured (its buffers are then in place: a step that would allocate returns
+ * HOTRG_ESTATE), and must carry no derivative, no known leg parities (the Z2
+ * parity read-back waits on the host: hotrg_set_parity(ctx, NULL) drops them),
+ * no phase timing and no shard step.  The context's state is left as it was.
+ * hotrg_graph_launch enqueues one replay on the context's stream (asynchronous)
+ * and advances the run by n steps: the same kernels with the same arguments as
+ * the uncaptured steps, so the results are the same bit for bit; the step
+ * count of the ln Z bookkeeping is read on the device.  A graph belongs to its
+ * context and may be launched only at the start of its cycle (ESTATE
+ * otherwise); free it before the context.  Errors: EINVAL, ESTATE, ECUDA. */
+typedef struct hotrg_graph hotrg_graph;
+int hotrg_graph_capture(hotrg_ctx* ctx, int n, const int* axes, int chi, hotrg_graph** out);
+int hotrg_graph_launch(hotrg_ctx* ctx, hotrg_graph* graph);
+void hotrg_graph_free(hotrg_graph* graph);
 
 /* c'-slice shard of one step over W ranks (processes, one GPU each), each holding
  * a context with the same local tensor (the paper's replication of T over its

@@ -89,6 +89,9 @@ def load():
         "hotrg_shard_finish": (I, [P, I, I, P, I64]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "hotrg_launch_count": (I, [P, ctypes.POINTER(I64)]),
+        "hotrg_graph_capture": (I, [P, I, ctypes.POINTER(I), I, ctypes.POINTER(P)]),
+        "hotrg_graph_launch": (I, [P, P]),
+        "hotrg_graph_free": (None, [P]),
         "hotrg_free": (None, [P]),
         "hotrg_strerror": (ctypes.c_char_p, [I]),
     }
@@ -246,9 +249,32 @@ def hotrg_set_z2(ctx, enable: bool):
 
 
 def hotrg_set_parity(ctx, parity):
-    """Declare the parities of every index (axis 0's indices first, then axis 1, ...)."""
+    """Declare the parities of every index (axis 0's indices first, then axis 1, ...);
+    None forgets them (dense steps, no read-back)."""
+    if parity is None:
+        _check(load().hotrg_set_parity(ctx, None), "hotrg_set_parity")
+        return
     arr = (ctypes.c_int * len(parity))(*[int(x) for x in parity])
     _check(load().hotrg_set_parity(ctx, arr), "hotrg_set_parity")
+
+
+def hotrg_graph_capture(ctx, axes, chi: int):
+    """Record the steps (axes[i], chi) into a CUDA graph without running them; returns
+    the graph handle (a closed sequence: see include/hotrg.h)."""
+    n = len(axes)
+    ax = (ctypes.c_int * n)(*[int(a) for a in axes])
+    g = ctypes.c_void_p()
+    _check(load().hotrg_graph_capture(ctx, n, ax, int(chi), ctypes.byref(g)), "hotrg_graph_capture")
+    return g
+
+
+def hotrg_graph_launch(ctx, graph):
+    """Enqueue one replay of the captured steps on the context's stream."""
+    _check(load().hotrg_graph_launch(ctx, graph), "hotrg_graph_launch")
+
+
+def hotrg_graph_free(graph):
+    load().hotrg_graph_free(graph)
 
 
 def hotrg_leg_parity(ctx):

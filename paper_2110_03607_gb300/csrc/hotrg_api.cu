@@ -197,12 +197,16 @@ struct hotrg_ctx {
   int shard_z2 = 0, shard_track = 0;
   double shard_bn_done = 0.0;
   std::vector<unsigned char> shard_par[kMaxD];
+  // set while hotrg_graph_capture records steps: no buffer may be (re)allocated and the
+  // normalisation takes the step count from the device
+  int capturing = 0;
 };
 
 namespace {
 
 int dev_alloc(hotrg_ctx* c, Buf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return HOTRG_OK;
+  if (c->capturing) return HOTRG_ESTATE;   // a captured step must find its buffers in place
   if (b.p) {
     if (c->ffn) c->ffn(b.p, c->user);
     else cudaFree(b.p);
@@ -430,7 +434,7 @@ void trace_and_normalise(hotrg_ctx* c, double* Tsrc, int first) {
   for (int s = 1; s < d; ++s) pn *= c->chis[c->order[s]];
   DevState* st = (DevState*)c->state.p;
   launch_trace_y(Tsrc, chi_c, pn, (double*)c->Y.p, c->stream);
-  launch_finish_step((double*)c->Y.p, chi_c, st, c->p, first, c->stream);
+  launch_finish_step((double*)c->Y.p, chi_c, st, c->capturing ? -1 : c->p, first, c->stream);
   launch_scale(Tsrc, (double*)c->T.p, tensor_elems(c), st, c->stream);
 }
 
@@ -2158,6 +2162,179 @@ int hotrg_gemm_nt(int mode, int M, int N, int K, const double* A, const double* 
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Captured steps (CUDA graph): the host state a step changes, so that a capture can
+// be undone and a replay can apply it
+// ---------------------------------------------------------------------------
+namespace {
+struct HostSnap {
+  int p, last_fp64, last_valid, last_nlegs, last_z2, poisoned;
+  int chis[kMaxD], order[kMaxD];
+  int last_leg_axis[kMaxD - 1], last_leg_n[kMaxD - 1], last_leg_nnew[kMaxD - 1];
+  long long last_lam_off[kMaxD - 1], last_u_off[kMaxD - 1];
+  double last_bn_dense, last_bn_done;
+  Buf T, T2;
+};
+
+HostSnap take_snap(const hotrg_ctx* c) {
+  HostSnap h;
+  h.p = c->p;
+  h.last_fp64 = c->last_fp64;
+  h.last_valid = c->last_valid;
+  h.last_nlegs = c->last_nlegs;
+  h.last_z2 = c->last_z2;
+  h.poisoned = c->poisoned;
+  for (int k = 0; k < kMaxD; ++k) {
+    h.chis[k] = c->chis[k];
+    h.order[k] = c->order[k];
+  }
+  for (int k = 0; k < kMaxD - 1; ++k) {
+    h.last_leg_axis[k] = c->last_leg_axis[k];
+    h.last_leg_n[k] = c->last_leg_n[k];
+    h.last_leg_nnew[k] = c->last_leg_nnew[k];
+    h.last_lam_off[k] = c->last_lam_off[k];
+    h.last_u_off[k] = c->last_u_off[k];
+  }
+  h.last_bn_dense = c->last_bn_dense;
+  h.last_bn_done = c->last_bn_done;
+  h.T = c->T;
+  h.T2 = c->T2;
+  return h;
+}
+
+// the step count and the records of the last step
+void put_step_records(hotrg_ctx* c, const HostSnap& h) {
+  c->p = h.p;
+  c->last_fp64 = h.last_fp64;
+  c->last_valid = h.last_valid;
+  c->last_nlegs = h.last_nlegs;
+  c->last_z2 = h.last_z2;
+  for (int k = 0; k < kMaxD - 1; ++k) {
+    c->last_leg_axis[k] = h.last_leg_axis[k];
+    c->last_leg_n[k] = h.last_leg_n[k];
+    c->last_leg_nnew[k] = h.last_leg_nnew[k];
+    c->last_lam_off[k] = h.last_lam_off[k];
+    c->last_u_off[k] = h.last_u_off[k];
+  }
+  c->last_bn_dense = h.last_bn_dense;
+  c->last_bn_done = h.last_bn_done;
+}
+
+bool same_layout(const hotrg_ctx* c, const HostSnap& h) {
+  for (int k = 0; k < kMaxD; ++k)
+    if (c->chis[k] != h.chis[k] || c->order[k] != h.order[k]) return false;
+  return c->T.p == h.T.p && c->T2.p == h.T2.p;
+}
+
+// a context whose steps may be captured: no derivative, no parity read-back, no
+// phase timing, no shard in progress
+int capture_ready(const hotrg_ctx* c) {
+  if (c->poisoned) return HOTRG_ESTATE;
+  if (c->tangent || c->z2_valid || c->profile || c->shard_ready) return HOTRG_ESTATE;
+  return HOTRG_OK;
+}
+}  // namespace
+
+struct hotrg_graph {
+  hotrg_ctx* owner = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nsteps = 0;
+  long long launches = 0;   // kernels of one replay
+  HostSnap after;           // the host state the captured steps leave
+};
+
+int hotrg_graph_capture(hotrg_ctx* c, int n, const int* axes, int chi, hotrg_graph** out) {
+  if (!c || !out || n < 1 || n > 64 || !axes || chi < 1 || chi > 32) return HOTRG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (axes[i] < 0 || axes[i] >= c->d) return HOTRG_EINVAL;
+  int r = capture_ready(c);
+  if (r != HOTRG_OK) return r;
+  if (pending_error(c, "work before the capture") != HOTRG_OK) return HOTRG_ECUDA;
+  // the legacy default stream cannot be captured: record on a stream of our own
+  cudaStream_t user_stream = c->stream, cs = c->stream;
+  if (cs == nullptr && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_status(c);
+  if (cudaStreamSynchronize(user_stream) != cudaSuccess) {
+    if (cs != user_stream) cudaStreamDestroy(cs);
+    return cuda_status(c);
+  }
+  const HostSnap before = take_snap(c);
+  const long long launches0 = g_launches;
+  c->stream = cs;
+  c->capturing = 1;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    r = HOTRG_ECUDA;
+  } else {
+    for (int i = 0; i < n && r == HOTRG_OK; ++i) r = step_impl(c, axes[i], chi, Shard());
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (r == HOTRG_OK && e != cudaSuccess) r = HOTRG_ECUDA;
+  }
+  c->capturing = 0;
+  c->stream = user_stream;
+  const long long captured = g_launches - launches0;
+  g_launches -= captured;   // nothing ran
+  const HostSnap after = take_snap(c);
+  // nothing of the captured steps ran: put the host state back
+  put_step_records(c, before);
+  for (int k = 0; k < kMaxD; ++k) {
+    c->chis[k] = before.chis[k];
+    c->order[k] = before.order[k];
+  }
+  c->T = before.T;
+  c->T2 = before.T2;
+  c->poisoned = before.poisoned;
+  cudaGetLastError();   // a refused capture leaves its error here
+  if (cs != user_stream) cudaStreamDestroy(cs);
+  // the sequence must end where it starts (bond dims, slot order, buffers), so that it
+  // can be replayed back to back
+  if (r == HOTRG_OK) {
+    bool closed = true;
+    for (int k = 0; k < kMaxD; ++k)
+      closed = closed && after.chis[k] == before.chis[k] && after.order[k] == before.order[k];
+    closed = closed && after.T.p == before.T.p && after.T2.p == before.T2.p;
+    if (!closed) r = HOTRG_ESTATE;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (r == HOTRG_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    r = HOTRG_ECUDA;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (r != HOTRG_OK) return r;
+  hotrg_graph* g = new hotrg_graph();
+  g->owner = c;
+  g->exec = exec;
+  g->nsteps = n;
+  g->launches = captured;
+  g->after = after;
+  *out = g;
+  return HOTRG_OK;
+}
+
+int hotrg_graph_launch(hotrg_ctx* c, hotrg_graph* g) {
+  if (!c || !g || g->owner != c) return HOTRG_EINVAL;
+  int r = capture_ready(c);
+  if (r != HOTRG_OK) return r;
+  if (!same_layout(c, g->after)) return HOTRG_ESTATE;   // not at the start of the captured cycle
+  if (cudaGraphLaunch(g->exec, c->stream) != cudaSuccess) {
+    cuda_status(c);
+    return HOTRG_ECUDA;
+  }
+  g_launches += g->launches;
+  HostSnap rec = g->after;
+  rec.p = c->p + g->nsteps;
+  put_step_records(c, rec);
+  return pending_error(c, "the graph launch");
+}
+
+void hotrg_graph_free(hotrg_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+}
+
 int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, int nthreads,
                      int* status) {
   if (n < 0 || (n > 0 && (!ctxs || !axes || !chis))) return HOTRG_EINVAL;
@@ -2195,8 +2372,13 @@ int hotrg_set_z2(hotrg_ctx* c, int enable) {
 }
 
 int hotrg_set_parity(hotrg_ctx* c, const int* parity) {
-  if (!c || !parity) return HOTRG_EINVAL;
+  if (!c) return HOTRG_EINVAL;
   if (c->poisoned) return HOTRG_ESTATE;
+  if (!parity) {   // forget them: dense steps from here on, with no read-back
+    c->z2_valid = 0;
+    for (int k = 0; k < kMaxD; ++k) c->par[k].clear();
+    return HOTRG_OK;
+  }
   const int d = c->d;
   std::vector<unsigned char> par[kMaxD];
   int off = 0;

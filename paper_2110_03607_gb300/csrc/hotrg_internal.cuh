@@ -23,7 +23,7 @@ struct DevState {
   double ln_z_site;    // ln Z^(p) / 2^p
   double gu_wen;       // X of the last new tensor
   int status;          // 0 or a negative hotrg_status
-  int pad;
+  int p;               // steps taken (the step count of the last normalisation)
 };
 
 // Device-side derivative state of a run (d/d beta, forward mode), beside DevState.

@@ -173,6 +173,9 @@ __global__ void finish_step_kernel(const double* __restrict__ Y, int chi_c, DevS
       st->inv_trace = 1.0;
       return;
     }
+    // p < 0: a step replayed from a captured graph takes its count from the device
+    if (p < 0) p = st->p + 1;
+    st->p = p;
     double ln_tr = log(tr);
     if (first) {
       st->kappa = 0.0;
