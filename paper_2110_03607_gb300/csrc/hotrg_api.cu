@@ -309,6 +309,10 @@ void* pinned_stage(hotrg_ctx* c, size_t bytes) {
 // Jacobi grid-barrier counters: 3 per matrix of one launch (up to 4 (d - 1) parity
 // blocks), then 3 for the FP32 warm start
 constexpr int kCounters32 = 3 * 4 * kMaxD;
+// the FP64 eigen-solver's per-matrix largest squared column norm (16 x 64 bits) after
+// the rotation counters of both solvers
+constexpr int kColmaxOff = kCounters32 + 4;
+constexpr int kCounterInts = kColmaxOff + 2 * 16;
 
 int num_sms() { return sm_count(); }
 
@@ -812,7 +816,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   CHECK_ALLOC(dev_alloc(c, c->J32, sizeof(float) * 2 * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Gns, sizeof(double) * total_mat_elems));
   CHECK_ALLOC(dev_alloc(c, c->Vtmp, sizeof(double) * total_mat_elems));
-  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (kCounters32 + 3)));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * kCounterInts));
   CHECK_ALLOC(dev_alloc(c, c->sweeps, sizeof(int) * 6 * kMaxD));
 
   // Gram of leg j, kind: X = T with the free pair (n_j or n'_j, c' or c) first, rest after
@@ -1074,7 +1078,8 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         Ainit = nullptr;
       }
     }
-    return launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p, sweeps_out,
+    return launch_jacobi(Wg, Vg, Ainit, n, cnt, 60, (int*)c->counters.p,
+                         (unsigned long long*)((int*)c->counters.p + kColmaxOff), sweeps_out,
                          (DevState*)c->state.p, s);
   };
   if (!env_phase) {
@@ -2398,7 +2403,7 @@ int hotrg_set_parity(hotrg_ctx* c, const int* parity) {
     sl.mask[k] = 0;
     for (int v = 0; v < c->chis[ax]; ++v) sl.mask[k] |= (unsigned)par[ax][v] << v;
   }
-  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * (kCounters32 + 3)));
+  CHECK_ALLOC(dev_alloc(c, c->counters, sizeof(int) * kCounterInts));
   int* cnt = (int*)c->counters.p;
   int bad = 0;
   cudaMemsetAsync(cnt, 0, sizeof(int), c->stream);

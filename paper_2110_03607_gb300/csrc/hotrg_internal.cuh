@@ -162,8 +162,10 @@ void launch_assemble_a(const double* s_hat, const double* s_chk, int chi_j, int 
                        double* A, cudaStream_t s);
 
 // ---- kernels_eig.cu
+// colmax: nmat (<= 16) words of scratch
 int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
-                  int* counters, int* sweeps_out, DevState* st, cudaStream_t s);
+                  int* counters, unsigned long long* colmax, int* sweeps_out, DevState* st,
+                  cudaStream_t s);
 int launch_jacobi32_block(const double* A, float* W32, float* V32, int n, int nmat,
                           int max_sweeps, int* counters, cudaStream_t s);
 void launch_widen_f32(const float* in, double* out, long long n, cudaStream_t s);

@@ -12,6 +12,16 @@
 // its own warp; rounds are separated by a grid-wide barrier of a cooperative
 // launch.  A pair whose inner product is exactly 0 is never rotated, which
 // keeps an exact Z2 block pattern of A exact.
+//
+// Stopping rule: a sweep counts only the rotations of pairs in which a column's
+// squared norm exceeds (4 n eps)^2 times the largest squared column norm at the
+// start (about lambda_1^2): the solver stops after a sweep that rotates no such
+// pair.  Pairs of two columns below that floor -- the near-null space of A, whose
+// columns are rounding noise of order n eps lambda_1 -- are still rotated as
+// before, but their mutual orthogonalisation no longer keeps the sweeps going:
+// every column above the floor is then orthogonal to every other column to the
+// rotation tolerance, so its vector is an eigenvector as before, and the columns
+// below it span the rest of the space (V stays orthogonal).
 #include <cooperative_groups.h>
 
 #include "hotrg_internal.cuh"
@@ -31,8 +41,8 @@ template <int NPL>
 __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double* V,
                                                                const double* __restrict__ A, int n,
                                                                int nmat, int max_sweeps,
-                                                               int* counters, int* sweeps_out,
-                                                               DevState* st) {
+                                                               int* counters, unsigned long long* colmax,
+                                                               int* sweeps_out, DevState* st) {
   cg::grid_group grid = cg::this_grid();
   const long long nn = (long long)n * n;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,6 +57,7 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
     }
   }
   if (gtid < 3 * nmat) counters[gtid] = 0;
+  if (gtid < nmat) colmax[gtid] = 0ull;
   grid.sync();
 
   const int mp = n + (n & 1);
@@ -57,6 +68,20 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
   const int gw = (int)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const int nw = (int)(gthreads >> 5);
   const int ntasks = nmat * npairs;
+  // largest squared column norm of every matrix (non-negative doubles order like their
+  // bit patterns, so an integer maximum is exact and independent of the order)
+  for (int task = gw; task < nmat * n; task += nw) {
+    const int mat = task / n, col = task % n;
+    const double* w = W + mat * nn + (long long)col * n;
+    double a = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double x = __ldcg(w + i);
+      a = fma(x, x, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0 && a > 0.0) atomicMax(colmax + mat, (unsigned long long)__double_as_longlong(a));
+  }
+  grid.sync();
   // the computed inner product carries rounding of order n eps sqrt(a b): a
   // tolerance below that level would keep rotating rounding noise forever.  A pair
   // is rotated only if |g| > tol max(a, b), not tol sqrt(a b): the rotation it would
@@ -101,6 +126,7 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
         const double big = fmax(a, b);
         bool rot = (g != 0.0) && big > 1e-280 && (fabs(g) > tol * big);
         if (!rot) continue;
+        const bool counts = big > tol * tol * __longlong_as_double((long long)__ldcg(colmax + mat));
         double zeta = (b - a) / (2.0 * g);
         double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t);
@@ -120,7 +146,7 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
           __stcg(vp + i, c * x - s * y);
           __stcg(vq + i, s * x + c * y);
         }
-        if (lane == 0) atomicAdd(cur + mat, 1);
+        if (lane == 0 && counts) atomicAdd(cur + mat, 1);
       }
       grid.sync();
     }
@@ -139,7 +165,8 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
 
 template <int NPL>
 static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
-                           int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
+                           int* counters, unsigned long long* colmax, int* sweeps_out, DevState* st,
+                           cudaStream_t s) {
   // resident CTAs per SM, queried once per device
   static std::atomic<int> per_cache[kMaxDevices];
   int dev = 0;
@@ -161,7 +188,7 @@ static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nma
   int blocks = tasks < s_sms ? tasks : s_sms;
   if (blocks > s_sms * s_per_sm) blocks = s_sms * s_per_sm;
   if (blocks < 1) blocks = 1;
-  void* args[] = {&W, &V, &A, &n, &nmat, &max_sweeps, &counters, &sweeps_out, &st};
+  void* args[] = {&W, &V, &A, &n, &nmat, &max_sweeps, &counters, &colmax, &sweeps_out, &st};
   cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_onesided_kernel<NPL>, dim3(blocks),
                                               dim3(256), args, 0, s);
   ++g_launches;
@@ -169,14 +196,18 @@ static int launch_jacobi_t(double* W, double* V, const double* A, int n, int nma
 }
 
 int launch_jacobi(double* W, double* V, const double* A, int n, int nmat, int max_sweeps,
-                  int* counters, int* sweeps_out, DevState* st, cudaStream_t s) {
-  int npl = (n + 31) / 32;
-  if (npl <= 1) return launch_jacobi_t<1>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
-  if (npl <= 2) return launch_jacobi_t<2>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
-  if (npl <= 4) return launch_jacobi_t<4>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
-  if (npl <= 8) return launch_jacobi_t<8>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
-  if (npl <= 16) return launch_jacobi_t<16>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
-  if (npl <= 32) return launch_jacobi_t<32>(W, V, A, n, nmat, max_sweeps, counters, sweeps_out, st, s);
+                  int* counters, unsigned long long* colmax, int* sweeps_out, DevState* st,
+                  cudaStream_t s) {
+  if (nmat > 16) return -1;
+  const int npl = (n + 31) / 32;
+#define HOTRG_JAC(P) return launch_jacobi_t<P>(W, V, A, n, nmat, max_sweeps, counters, colmax, sweeps_out, st, s)
+  if (npl <= 1) HOTRG_JAC(1);
+  if (npl <= 2) HOTRG_JAC(2);
+  if (npl <= 4) HOTRG_JAC(4);
+  if (npl <= 8) HOTRG_JAC(8);
+  if (npl <= 16) HOTRG_JAC(16);
+  if (npl <= 32) HOTRG_JAC(32);
+#undef HOTRG_JAC
   return -1;
 }
 

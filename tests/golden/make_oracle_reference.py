@@ -24,6 +24,9 @@ WORKLOADS = {
     "ising2d_chi8": dict(d=2, beta=0.4406868, h=0.0, chi=8, steps=20, first=0),
     # 4D Ising, chi = 6, cycling x, y, z, w
     "ising4d_chi6": dict(d=4, beta=0.15, h=0.0, chi=6, steps=12, first=0),
+    # 2D Ising, chi = 24, beta = 0.3 (ordered phase), alternating x, y: near-null
+    # environments (about 530 of 576 eigenvalues below 1e-15 lambda_1)
+    "ising2d_chi24_b03": dict(d=2, beta=0.3, h=0.0, chi=24, steps=20, first=0),
     # 3D Ising, chi = 20, through step 7 (a steady step costs ~4e14 flop on the CPU: ~35 min)
     "ising3d_chi20": dict(d=3, beta=0.2216544, h=0.0, chi=20, steps=7, first=2),
 }

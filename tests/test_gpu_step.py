@@ -388,3 +388,34 @@ def test_ising3d_chi20_free_energy_matches_oracle_reference(pkg):
                 assert not pkg.hotrg_step_times(g.ctx)[2], step
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("z2", [True, False])
+def test_ising2d_chi24_ordered_phase_matches_oracle_reference(pkg, z2):
+    # 2D Ising chi = 24 at beta = 0.3: the environments have a near-null space of about
+    # 530 of 576 directions (rounding noise); the FP64 form must converge on every step
+    # and follow the oracle's reference (tests/golden/ising2d_chi24_b03.jsonl) to 1e-12
+    gold = _golden("ising2d_chi24_b03")
+    assert max(gold) == 20
+    g = pkg.Hotrg(2, 0.3, 0.0, precision=pkg.PREC_FP64, z2=z2)
+    # At step 11 the cut falls inside a degenerate pair (gap at the cut 2.8e-15 lambda_1):
+    # the kept 24th vector is then any combination of the two, and from the next step on
+    # the oracle's and the GPU's tensors are different valid results.  ln Z / V stays
+    # unique (gated at 1e-12 throughout); the spectra are gated at 1e-12 lambda_1 until
+    # a cut is degenerate, at 1e-8 lambda_1 after it (measured: 6.7e-10 at step 12).
+    unique = True
+    try:
+        for step in range(1, 21):
+            g.step((step - 1) % 2, 24)
+            lnz, _ = g.free_energy()      # raises on a sweep cap (ENOTCONV)
+            ref = gold[step]["ln_z_per_site"]
+            assert abs(lnz - ref) <= 1e-12 * abs(ref), (step, lnz, ref)
+            for leg in gold[step]["legs"]:
+                lam = pkg.hotrg_spectrum(g.ctx, leg["axis"], 0)
+                want = np.array(leg["lam"])
+                np.testing.assert_allclose(lam[: len(want)], want, rtol=0,
+                                           atol=(1e-12 if unique else 1e-8) * want[0],
+                                           err_msg=f"step {step} leg {leg['axis']}")
+            unique = unique and all(leg["gap"] is None or leg["gap"] > 1e-13 for leg in gold[step]["legs"])
+    finally:
+        g.close()
