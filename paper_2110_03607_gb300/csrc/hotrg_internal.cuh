@@ -187,7 +187,9 @@ void launch_chain_f64(const ChainDesc& d, const double* in, const double* U, dou
                       cudaStream_t s);
 void launch_chain_f64acc(const ChainDesc& d, const void* in, int in_is_f64, const double* U,
                          void* out, int out_mode, cudaStream_t s);
-enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2, OUT_Z2_SPLIT = 3 };
+// OUT_Z2_SPLIT_W: OUT_Z2_SPLIT for K lists whose length R is a multiple of 32 (every
+// warp full, its threads in one row group of the output)
+enum { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16_SPLIT = 2, OUT_Z2_SPLIT = 3, OUT_Z2_SPLIT_W = 4 };
 
 // Last prime stage written straight into the Z2 blocks of the bottleneck's B operand.
 // The stage's out view is the dense B (row (n', n~) x kpad + k, k = (rho, n^')), whose

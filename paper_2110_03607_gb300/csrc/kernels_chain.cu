@@ -39,9 +39,18 @@ struct URow<float, NN> {
 };
 
 // The stages that read the Z2 blocks of C and write those of B are held to three and
-// four CTAs per SM (80 and 64 registers): both are bound by memory latency
+// four CTAs per SM (80 and 64 registers): both are bound by memory latency.  Wider
+// accumulator rows (24, 32 outputs) or FP64 inputs take three or two, without spills.
+template <typename TIn, int NN, int OUT, bool ZIN>
+constexpr int chain_min_ctas() {
+  return ZIN ? (NN <= 16 ? 3 : 2)
+             : (OUT == OUT_Z2_SPLIT || OUT == OUT_Z2_SPLIT_W)
+                   ? (NN <= 16 ? (sizeof(TIn) == 4 ? 4 : 3) : (NN <= 24 && sizeof(TIn) == 4 ? 3 : 2))
+                   : 1;
+}
+
 template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
-__global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
+__global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
                                                     const TAcc* __restrict__ U, void* out, Z2In zi,
                                                     Z2Out zo) {
   extern __shared__ __align__(16) unsigned char smem_u[];
@@ -57,7 +66,7 @@ __global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) 
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d.total; t += stride) {
     unsigned rem = (unsigned)t;
     unsigned kidx = 0;
-    if (OUT == OUT_Z2_SPLIT) {
+    if (OUT == OUT_Z2_SPLIT || OUT == OUT_Z2_SPLIT_W) {
       // t = (row group, list position): the thread's dense k comes from the K lists
       const unsigned grp = rem / zo.R;
       kidx = rem - grp * zo.R;
@@ -75,6 +84,17 @@ __global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) 
       in_off += (long long)idx * d.in_stride[k];
       out_off += (long long)idx * d.out_stride[k];
       if (k == d.a_dim) a_val = (int)idx;
+    }
+    // OUT_Z2_SPLIT_W: the warp's threads share the output rows row0 + n nrow_step; lane n
+    // reads the packed (position | block << 31) of row n now, so that the lookups'
+    // latency hides behind the multiply-adds, and the stores take them by shuffle
+    unsigned zlane = 0u;
+    if (OUT == OUT_Z2_SPLIT_W) {
+      const int ln = threadIdx.x & 31;
+      if (ln < NN && ln < d.nn) {
+        const long long row = out_off / zo.kpad + ln * zo.nrow_step;
+        zlane = (unsigned)zo.cpos[row] | ((unsigned)(zo.cblk[row] ^ zo.q) << 31);
+      }
     }
     TAcc acc[NN];
 #pragma unroll
@@ -188,7 +208,25 @@ __global__ void __launch_bounds__(256, ZIN ? 3 : (OUT == OUT_Z2_SPLIT ? 4 : 1)) 
       // selects, not an index: an indexed parameter array would be copied to local memory
       void* ob = kb ? zo.blk[1] : zo.blk[0];
       const long long ld = kb ? zo.ld[1] : zo.ld[0], ps = kb ? zo.pstride[1] : zo.pstride[0];
-      if (d.pfmt == PIECE_TF32) {
+      if (OUT == OUT_Z2_SPLIT_W) {
+        if (d.pfmt == PIECE_TF32) {
+#pragma unroll
+          for (int n = 0; n < NN; ++n) {
+            if (n >= d.nn) break;
+            const unsigned z = __shfl_sync(0xffffffffu, zlane, n);
+            if ((int)(z >> 31) != kb) continue;
+            store_pieces_as<PIECE_TF32>(ob, kpos + (long long)(z & 0x7fffffffu) * ld, ps, d.npieces, acc[n]);
+          }
+        } else {
+#pragma unroll
+          for (int n = 0; n < NN; ++n) {
+            if (n >= d.nn) break;
+            const unsigned z = __shfl_sync(0xffffffffu, zlane, n);
+            if ((int)(z >> 31) != kb) continue;
+            store_pieces_as<PIECE_BF16>(ob, kpos + (long long)(z & 0x7fffffffu) * ld, ps, d.npieces, acc[n]);
+          }
+        }
+      } else if (d.pfmt == PIECE_TF32) {
 #pragma unroll
         for (int n = 0; n < NN; ++n) {
           if (n >= d.nn) break;
@@ -258,20 +296,29 @@ void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, v
   else dispatch_nn_z2in<OUT_F32>(d, zi, U, out, s);
 }
 
-template <typename TIn>
+template <typename TIn, int OUT>
 static void dispatch_nn_z2out(const ChainDesc& d, const TIn* in, const float* U, const Z2Out& zo, cudaStream_t s) {
   const Z2In none{};
-  if (d.nn <= 4) launch_one<TIn, float, 4, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
-  else if (d.nn <= 8) launch_one<TIn, float, 8, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
-  else if (d.nn <= 16) launch_one<TIn, float, 16, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
-  else if (d.nn <= 24) launch_one<TIn, float, 24, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
-  else launch_one<TIn, float, 32, OUT_Z2_SPLIT>(d, in, U, nullptr, s, none, zo);
+  if (d.nn <= 4) launch_one<TIn, float, 4, OUT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 8) launch_one<TIn, float, 8, OUT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 16) launch_one<TIn, float, 16, OUT>(d, in, U, nullptr, s, none, zo);
+  else if (d.nn <= 24) launch_one<TIn, float, 24, OUT>(d, in, U, nullptr, s, none, zo);
+  else launch_one<TIn, float, 32, OUT>(d, in, U, nullptr, s, none, zo);
 }
 
 void launch_chain_f32_z2out(const ChainDesc& d, const void* in, int in_is_f64, const float* U, const Z2Out& zo,
                             cudaStream_t s) {
-  if (in_is_f64) dispatch_nn_z2out<double>(d, (const double*)in, U, zo, s);
-  else dispatch_nn_z2out<float>(d, (const float*)in, U, zo, s);
+  // R a multiple of 32: thread t of the grid covers list position t % R of row group
+  // t / R, so the 32 threads of a warp share the row group, and d.total (row groups x R)
+  // leaves no warp partly filled
+  const bool warp_rows = zo.R % 32u == 0;
+  if (in_is_f64) {
+    if (warp_rows) dispatch_nn_z2out<double, OUT_Z2_SPLIT_W>(d, (const double*)in, U, zo, s);
+    else dispatch_nn_z2out<double, OUT_Z2_SPLIT>(d, (const double*)in, U, zo, s);
+  } else {
+    if (warp_rows) dispatch_nn_z2out<float, OUT_Z2_SPLIT_W>(d, (const float*)in, U, zo, s);
+    else dispatch_nn_z2out<float, OUT_Z2_SPLIT>(d, (const float*)in, U, zo, s);
+  }
 }
 
 void launch_chain_f32(const ChainDesc& d, const void* in, int in_is_f64, const float* U, void* out,
