@@ -49,7 +49,10 @@ constexpr int chain_min_ctas() {
                    : 1;
 }
 
-template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
+// ZW (with ZIN): the 32 threads of a warp read the same rows of C (the host checks the
+// thread dims: the leading dims without a row stride span a multiple of 32 threads, and
+// so does the total); lane a then reads row a's block and position once, before the sums
+template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false, bool ZW = false>
 __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) chain_kernel(ChainDesc d, const TIn* __restrict__ in,
                                                     const TAcc* __restrict__ U, void* out, Z2In zi,
                                                     Z2Out zo) {
@@ -114,6 +117,14 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
       // are nonzero; same two-level sums
       const long long row0 = in_off >> 32, kar = d.ka_stride >> 32;
       const long long col0 = in_off & 0xffffffffLL;
+      unsigned zr = 0u;
+      if (ZW) {
+        const int ln = threadIdx.x & 31;
+        if (ln < d.chi) {
+          const long long row = row0 + ln * kar;
+          zr = (unsigned)zi.rpos[row] | ((unsigned)zi.rblk[row] << 31);
+        }
+      }
       // the column maps do not depend on a: for chi <= 16 read them once, packed as
       // position | (block of the column) << 31
       unsigned cpk[16];
@@ -130,11 +141,20 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
         }
       }
       for (int a = a_lo; a < a_hi; ++a) {
-        const long long row = row0 + a * kar;
-        const int rb = zi.rblk[row];
+        int rb;
+        long long rp;
+        if (ZW) {   // warp-uniform: the continue below is taken by the whole warp
+          const unsigned z = __shfl_sync(0xffffffffu, zr, a);
+          rb = (int)(z >> 31);
+          rp = (long long)(z & 0x7fffffffu);
+        } else {
+          const long long row = row0 + a * kar;
+          rb = zi.rblk[row];
+          rp = zi.rpos[row];
+        }
         const float* cr = rb ? zi.c[1] : zi.c[0];
         if (!cr) continue;
-        cr += (long long)zi.rpos[row] * zi.ld;
+        cr += rp * zi.ld;
         TAcc part[NN];
 #pragma unroll
         for (int n = 0; n < NN; ++n) part[n] = TAcc(0);
@@ -247,18 +267,18 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
   }
 }
 
-template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false>
+template <typename TIn, typename TAcc, int NN, int OUT, bool ZIN = false, bool ZW = false>
 static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* out, cudaStream_t s,
                        const Z2In& zi = Z2In{}, const Z2Out& zo = Z2Out{}) {
   size_t smem = (size_t)d.chi * d.chi * URow<TAcc, NN>::ld * sizeof(TAcc);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT, ZIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT, ZIN, ZW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   long long blocks = (d.total + 255) / 256;
   const long long cap = 16LL * sm_count();
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  chain_kernel<TIn, TAcc, NN, OUT, ZIN><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi, zo);
+  chain_kernel<TIn, TAcc, NN, OUT, ZIN, ZW><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi, zo);
   ++g_launches;
 }
 
@@ -280,20 +300,31 @@ static void dispatch_nn(const ChainDesc& d, const TIn* in, const TAcc* U, void* 
   else dispatch_out<TIn, TAcc, 32>(d, in, U, out, out_mode, s);
 }
 
-template <int OUT>
+template <int OUT, bool ZW>
 static void dispatch_nn_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, cudaStream_t s) {
   const float* none = nullptr;
-  if (d.nn <= 4) launch_one<float, float, 4, OUT, true>(d, none, U, out, s, zi);
-  else if (d.nn <= 8) launch_one<float, float, 8, OUT, true>(d, none, U, out, s, zi);
-  else if (d.nn <= 16) launch_one<float, float, 16, OUT, true>(d, none, U, out, s, zi);
-  else if (d.nn <= 24) launch_one<float, float, 24, OUT, true>(d, none, U, out, s, zi);
-  else launch_one<float, float, 32, OUT, true>(d, none, U, out, s, zi);
+  if (d.nn <= 4) launch_one<float, float, 4, OUT, true, ZW>(d, none, U, out, s, zi);
+  else if (d.nn <= 8) launch_one<float, float, 8, OUT, true, ZW>(d, none, U, out, s, zi);
+  else if (d.nn <= 16) launch_one<float, float, 16, OUT, true, ZW>(d, none, U, out, s, zi);
+  else if (d.nn <= 24) launch_one<float, float, 24, OUT, true, ZW>(d, none, U, out, s, zi);
+  else launch_one<float, float, 32, OUT, true, ZW>(d, none, U, out, s, zi);
 }
 
 void launch_chain_f32_z2in(const ChainDesc& d, const Z2In& zi, const float* U, void* out, int out_mode,
                            cudaStream_t s) {
-  if (out_mode == OUT_F64) dispatch_nn_z2in<OUT_F64>(d, zi, U, out, s);
-  else dispatch_nn_z2in<OUT_F32>(d, zi, U, out, s);
+  // warp-uniform rows of C: thread t's leading indices (those without a row stride)
+  // span p0 threads; with p0 and the total multiples of 32 every warp is full and its
+  // threads differ only in those indices
+  long long p0 = 1;
+  for (int k = 0; k < d.ndim && (d.in_stride[k] >> 32) == 0; ++k) p0 *= d.size[k];
+  const bool zw = p0 % 32 == 0 && d.total % 32 == 0 && d.chi <= 32;
+  if (out_mode == OUT_F64) {
+    if (zw) dispatch_nn_z2in<OUT_F64, true>(d, zi, U, out, s);
+    else dispatch_nn_z2in<OUT_F64, false>(d, zi, U, out, s);
+  } else {
+    if (zw) dispatch_nn_z2in<OUT_F32, true>(d, zi, U, out, s);
+    else dispatch_nn_z2in<OUT_F32, false>(d, zi, U, out, s);
+  }
 }
 
 template <typename TIn, int OUT>
