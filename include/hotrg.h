@@ -282,9 +282,25 @@ int hotrg_shard_finish(hotrg_ctx* ctx, int axis, int chi, const double* slices, 
  * once per step for the isometry choice.
  * enable = 1 needs a context from hotrg_init_ising with beta > 0 and no step
  * yet (dT^(0) is the beta-derivative of Eq. 2.4); enable = 0 stops carrying
- * it.  hotrg_set_tensor turns it off.  Errors: EINVAL (not an Ising context,
- * beta = 0, steps already taken), ENOMEM, ECUDA, ESTATE. */
+ * it.  hotrg_set_tensor turns it off.
+ * enable = 2 carries d2T = d^2 T / d beta^2 as well, in the FP64 form only
+ * (precision HOTRG_PREC_FP64, which then cannot be changed), with dense Grams
+ * and eigen-solver: every bilinear stage adds f(d2X, Y) + 2 f(dX, dY) +
+ * f(X, d2Y), and the kept isometry its second derivative in the parallel-
+ * transport gauge, d2U = P'' U + P' P' U, P' and P'' the derivatives of the
+ * projector on the kept eigenvectors (in the eigenbasis: divided differences
+ * of the kept-set indicator times V^T dA V and V^T d2A V; terms across a
+ * degenerate cut left out as in the first order).  hotrg_specific_heat then
+ * returns d^2(ln Z/V)/d beta^2.  A step costs about ten dense FP64 forward
+ * steps.  Errors: EINVAL (not an Ising context, beta = 0, steps already
+ * taken, enable = 2 with a split precision), ENOMEM, ECUDA, ESTATE. */
 int hotrg_set_tangent(hotrg_ctx* ctx, int enable);
+
+/* After synchronising: *d2lnz_dbeta2 = d^2(ln Z^(p) / 2^p)/d beta^2 of the
+ * last step and *specific_heat = beta^2 times it (the specific heat per site).
+ * Any out-pointer may be NULL.  Errors: EINVAL, ESTATE (second order not
+ * carried: hotrg_set_tangent(ctx, 2)), a recorded device failure. */
+int hotrg_specific_heat(hotrg_ctx* ctx, double* d2lnz_dbeta2, double* specific_heat);
 
 /* After synchronising: *dlnz_dbeta = d(ln Z^(p) / 2^p)/d beta of the last
  * step (of T^(0) before any step), *energy = its negative (the internal

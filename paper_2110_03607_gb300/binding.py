@@ -78,6 +78,7 @@ def load():
         "hotrg_bottleneck_flops": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
         "hotrg_set_tangent": (I, [P, I]),
         "hotrg_energy": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "hotrg_specific_heat": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "hotrg_tangent_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
         "hotrg_profile": (I, [P, I]),
         "hotrg_step_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -297,9 +298,18 @@ def hotrg_bottleneck_flops(ctx):
     return dense.value, done.value, bool(z2.value)
 
 
-def hotrg_set_tangent(ctx, enable: bool = True):
-    """Carry dT/d beta through the later steps (Ising context, before the first step)."""
-    _check(load().hotrg_set_tangent(ctx, 1 if enable else 0), "hotrg_set_tangent")
+def hotrg_set_tangent(ctx, enable=True):
+    """Carry dT/d beta through the later steps (Ising context, before the first step);
+    enable = 2 carries d^2 T / d beta^2 as well (FP64 form)."""
+    order = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+    _check(load().hotrg_set_tangent(ctx, order), "hotrg_set_tangent")
+
+
+def hotrg_specific_heat(ctx):
+    """(d^2(ln Z/V)/d beta^2, specific heat per site beta^2 d^2(ln Z/V)/d beta^2) of the last step."""
+    g2, c = ctypes.c_double(), ctypes.c_double()
+    _check(load().hotrg_specific_heat(ctx, ctypes.byref(g2), ctypes.byref(c)), "hotrg_specific_heat")
+    return g2.value, c.value
 
 
 def hotrg_energy(ctx):
@@ -463,6 +473,9 @@ class Hotrg:
 
     def energy(self):
         return hotrg_energy(self.ctx)
+
+    def specific_heat(self):
+        return hotrg_specific_heat(self.ctx)
 
     def close(self):
         if self.ctx:

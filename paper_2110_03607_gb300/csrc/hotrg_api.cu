@@ -189,6 +189,8 @@ struct hotrg_ctx {
   Buf dT, dT2, dTb, dXp, dS, dA, dU64, eG, eZ, eZt, rank, Yd, tstate;
   Buf dchA, dchB, dchT, dBp, tBp, dCb, tCb;
   Buf dAp, dB64, dU32;   // split-BF16 form: pieces of dT, FP64 staging of dB, dU in FP32
+  // tangent == 2: d2T = d^2 T / d beta^2 carried too (FP64 form), and its workspaces
+  Buf d2T, d2T2, d2Tb, d2Tc, d2Xp, d2S, d2A, d2U64, eG1, eW, eZ2, eZ2t, d2chA, d2chB, d2Bp, d2Cb, Yd2, parts2;
   // c'-slice shard of a step (hotrg_shard_*): the isometries of (shard_axis, shard_chi)
   // are installed and the new-leg parities derived from them are kept until the
   // gathered new tensor is installed
@@ -457,6 +459,22 @@ void tangent_trace_and_normalise(hotrg_ctx* c, const double* dTsrc, int first) {
   launch_tangent_scale(dTsrc, (const double*)c->T.p, (double*)c->dT.p, tensor_elems(c), st, tst, c->stream);
 }
 
+// The second order, after tangent_trace_and_normalise has run: d2 ln Tr, the d^2/d beta^2
+// of the ln Z bookkeeping, and c->d2T = d^2(T / Tr T) from d2Tsrc and dTsrc of the new,
+// unnormalised tensor and the normalised c->dT, c->T.
+void tangent2_trace_and_normalise(hotrg_ctx* c, const double* d2Tsrc, const double* dTsrc, int first) {
+  int d = c->d;
+  int chi_c = c->chis[c->order[0]];
+  long long pn = 1;
+  for (int s = 1; s < d; ++s) pn *= c->chis[c->order[s]];
+  const DevState* st = (const DevState*)c->state.p;
+  TanState* tst = (TanState*)c->tstate.p;
+  launch_trace_y(d2Tsrc, chi_c, pn, (double*)c->Yd2.p, c->stream);
+  launch_finish_tangent2((const double*)c->Yd2.p, chi_c, st, tst, c->p, first, c->stream);
+  launch_tangent2_scale(d2Tsrc, dTsrc, (const double*)c->dT.p, (const double*)c->T.p, (double*)c->d2T.p,
+                        tensor_elems(c), st, tst, c->stream);
+}
+
 int start_run(hotrg_ctx* c) {
   CHECK_ALLOC(dev_alloc(c, c->state, sizeof(DevState)));
   CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
@@ -599,11 +617,11 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   if (!c || (!alloc) != (!free_fn)) return HOTRG_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_status(c);
   // keep the tensor and the run state (and their derivatives), drop every workspace
-  Buf keep[4] = {c->T, c->state, c->dT, c->tstate};
-  size_t keep_bytes[4] = {c->T.bytes, c->state.bytes, c->tangent ? c->dT.bytes : 0,
-                          c->tangent ? c->tstate.bytes : 0};
-  std::vector<char> host[4];
-  for (int i = 0; i < 4; ++i) {
+  Buf keep[5] = {c->T, c->state, c->dT, c->tstate, c->d2T};
+  size_t keep_bytes[5] = {c->T.bytes, c->state.bytes, c->tangent ? c->dT.bytes : 0,
+                          c->tangent ? c->tstate.bytes : 0, c->tangent == 2 ? c->d2T.bytes : 0};
+  std::vector<char> host[5];
+  for (int i = 0; i < 5; ++i) {
     host[i].resize(keep_bytes[i]);
     if (keep_bytes[i] && keep[i].p &&
         cudaMemcpy(host[i].data(), keep[i].p, keep_bytes[i], cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -616,15 +634,17 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
               &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
               &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
               &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
-              &c->tCb, &c->dAp, &c->dB64, &c->dU32};
+              &c->tCb, &c->dAp, &c->dB64, &c->dU32, &c->d2T, &c->d2T2, &c->d2Tb, &c->d2Tc, &c->d2Xp,
+              &c->d2S, &c->d2A, &c->d2U64, &c->eG1, &c->eW, &c->eZ2, &c->eZ2t, &c->d2chA, &c->d2chB,
+              &c->d2Bp, &c->d2Cb, &c->Yd2, &c->parts2};
   n = (int)(sizeof(b) / sizeof(b[0]));
   for (int i = 0; i < n; ++i) dev_release(c, *b[i]);
   c->afn = alloc;
   c->ffn = free_fn;
   c->user = user;
   c->last_valid = 0;
-  Buf* kb[4] = {&c->T, &c->state, &c->dT, &c->tstate};
-  for (int i = 0; i < 4; ++i) {
+  Buf* kb[5] = {&c->T, &c->state, &c->dT, &c->tstate, &c->d2T};
+  for (int i = 0; i < 5; ++i) {
     if (!keep_bytes[i]) continue;
     CHECK_ALLOC(dev_alloc(c, *kb[i], keep_bytes[i]));
     if (cudaMemcpy(kb[i]->p, host[i].data(), keep_bytes[i], cudaMemcpyHostToDevice) != cudaSuccess)
@@ -632,11 +652,13 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   }
   CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
   if (c->tangent) CHECK_ALLOC(dev_alloc(c, c->Yd, sizeof(double) * kMaxBond * kMaxBond));
+  if (c->tangent == 2) CHECK_ALLOC(dev_alloc(c, c->Yd2, sizeof(double) * kMaxBond * kMaxBond));
   return HOTRG_OK;
 }
 
 int hotrg_set_precision(hotrg_ctx* c, int mode) {
   if (!c || mode < HOTRG_PREC_FP64 || mode > HOTRG_PREC_TF32X3) return HOTRG_EINVAL;
+  if (c->tangent == 2 && mode != HOTRG_PREC_FP64) return HOTRG_EINVAL;   // second order: FP64 form
   if (mode != HOTRG_PREC_FP64 && !tc_gemm_ready()) return HOTRG_ECUDA;
   c->precision = mode;
   return HOTRG_OK;
@@ -697,7 +719,9 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   const double bn_flops = 2.0 * (double)R * (double)R * (double)Pn * (double)P * (double)chi_c;
   // the derivative d/d beta, when carried, runs with the dense contraction
   const bool tangent = c->tangent != 0;
+  const bool tan2 = c->tangent == 2;   // d^2 / d beta^2 carried too (FP64 form)
   const bool fp64 = c->precision == HOTRG_PREC_FP64 || bn_flops < c->fp64_below;
+  if (tan2 && !fp64) return HOTRG_EINVAL;
   c->last_fp64 = fp64 ? 1 : 0;
 
   if (c->profile != 2) {   // profile 2 keeps the marks of several steps
@@ -717,6 +741,11 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
       CHECK_ALLOC(dev_alloc(c, c->dT2, sizeof(double) * RR));
       permute_slots(c, (const double*)c->dT.p, c->order, (double*)c->dT2.p, to, 1.0);
       std::swap(c->dT, c->dT2);
+    }
+    if (tan2) {
+      CHECK_ALLOC(dev_alloc(c, c->d2T2, sizeof(double) * RR));
+      permute_slots(c, (const double*)c->d2T.p, c->order, (double*)c->d2T2.p, to, 1.0);
+      std::swap(c->d2T, c->d2T2);
     }
     Tc = (double*)c->T.p;
     for (int k = 0; k < d; ++k) c->order[k] = to[k];
@@ -842,7 +871,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
   };
   // Z2 blocks of the Grams: the rows (free pair) and the summed index, both listed even
   // parity first, as element offsets into T; per leg the block and position of each row
-  const bool z2g = c->z2_valid && c->z2_enabled;
+  const bool z2g = c->z2_valid && c->z2_enabled && c->tangent != 2;
   const bool env_phase = phase == PH_FULL || phase == PH_ENV || phase == PH_ISO;
   long long gz_roff[kMaxD][4], gz_koff[kMaxD][4], gz_rowmap[kMaxD];
   long long gz_mb[kMaxD][2], gz_Kb[kMaxD][4][2], gz_n64 = 0, gz_eig[kMaxD];
@@ -1278,6 +1307,19 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     CHECK_ALLOC(dev_alloc(c, c->eG, sizeof(double) * eig_max));
     CHECK_ALLOC(dev_alloc(c, c->eZ, sizeof(double) * eig_max));
     CHECK_ALLOC(dev_alloc(c, c->eZt, sizeof(double) * eig_max));
+    long long nmax2 = 1;
+    for (int j = 1; j < d; ++j) nmax2 = std::max<long long>(nmax2, (long long)chij[j] * chij[j] * chij[j] * chij[j]);
+    if (tan2) {
+      CHECK_ALLOC(dev_alloc(c, c->d2Xp, sizeof(double) * RR));
+      CHECK_ALLOC(dev_alloc(c, c->d2S, sizeof(double) * 4 * nlegs * mmax * mmax));
+      CHECK_ALLOC(dev_alloc(c, c->d2A, sizeof(double) * total_mat_elems));
+      CHECK_ALLOC(dev_alloc(c, c->d2U64, sizeof(double) * u_total));
+      CHECK_ALLOC(dev_alloc(c, c->eG1, sizeof(double) * nmax2));
+      CHECK_ALLOC(dev_alloc(c, c->eW, sizeof(double) * nmax2));
+      CHECK_ALLOC(dev_alloc(c, c->eZ2, sizeof(double) * eig_max));
+      CHECK_ALLOC(dev_alloc(c, c->eZ2t, sizeof(double) * eig_max));
+      CHECK_ALLOC(dev_alloc(c, c->parts2, c->parts.bytes * 2));
+    }
     TanState* tst = (TanState*)c->tstate.p;
     for (int j = 1; j < d; ++j) {
       const long long m = (long long)chij[j] * chi_c;
@@ -1320,6 +1362,18 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         const int used = launch_gemm_nt_f64((const double*)c->dXp.p, K, (const double*)c->Xp.p, K,
                                             (double*)c->parts.p, m, m * m, (int)m, (int)m, K, nsplit, 0, s);
         launch_sym_sum((const double*)c->parts.p, used, (int)m, dS0 + kind * mmax * mmax, s);
+        if (tan2) {
+          // d2S = d2X X^T + X d2X^T + 2 dX dX^T: the partials of d2X X^T and of dX dX^T (each
+          // partial of the latter symmetric) summed with their transposes in one pass
+          double* d2S0 = (double*)c->d2S.p + ((long long)(j - 1) * 4) * mmax * mmax;
+          launch_permute((const double*)c->d2T.p, (double*)c->d2Xp.p, nd, size, ist, 1.0, s);
+          double* p2 = (double*)c->parts2.p;
+          const int u1 = launch_gemm_nt_f64((const double*)c->d2Xp.p, K, (const double*)c->Xp.p, K, p2, m, m * m,
+                                            (int)m, (int)m, K, nsplit, 0, s);
+          const int u2 = launch_gemm_nt_f64((const double*)c->dXp.p, K, (const double*)c->dXp.p, K,
+                                            p2 + (long long)u1 * m * m, m, m * m, (int)m, (int)m, K, nsplit, 0, s);
+          launch_sym_sum(p2, u1 + u2, (int)m, d2S0 + kind * mmax * mmax, s);
+        }
       }
       const double* S0 = (const double*)c->S.p + ((long long)(j - 1) * 4) * mmax * mmax;
       const long long k0 = 2 * side;
@@ -1336,6 +1390,24 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
                         tst, s);
       launch_gemm_nn_f64((const double*)c->eZt.p, n, Vs, n, G, n, nn, n, n, 1, 0, 0, 0, s);   // dU^T
       launch_transpose(G, nn, n, (double*)c->dU64.p + u_off[j], s);
+      if (tan2) {
+        // d2A, then d2U = V^T Z2 with Z2 from the projector's second derivative (eig_d2):
+        // G1 = V dA V^T over the unsorted eigenvectors, Gs = eZ (v_i . dA u_k), G2s = V d2A U
+        const double* d2S0 = (const double*)c->d2S.p + ((long long)(j - 1) * 4) * mmax * mmax;
+        double* d2As = (double*)c->d2A.p + mat_elem_off[2 * j + side];
+        launch_assemble_ddot(S0 + k0 * mmax * mmax, dS0 + k0 * mmax * mmax, d2S0 + k0 * mmax * mmax,
+                             S0 + (k0 + 1) * mmax * mmax, dS0 + (k0 + 1) * mmax * mmax,
+                             d2S0 + (k0 + 1) * mmax * mmax, chij[j], chi_c, d2As, s);
+        launch_gemm_nn_f64(Vs, n, dAs, n, (double*)c->eW.p, n, n, n, n, 1, 0, 0, 0, s);       // rows dA v_a
+        launch_gemm_nt_f64((const double*)c->eW.p, n, Vs, n, (double*)c->eG1.p, n, 0, n, n, n, 1, 0, s);
+        launch_gemm_nn_f64(d2As, n, (const double*)c->U64.p + u_off[j], nn, G, nn, n, nn, n, 1, 0, 0, 0, s);
+        launch_gemm_nn_f64(Vs, n, G, nn, (double*)c->eZ2.p, nn, n, nn, n, 1, 0, 0, 0, s);    // v_i . d2A u_k
+        launch_eig_d2((const double*)c->eG1.p, (const double*)c->eZ.p, (const double*)c->eZ2.p,
+                      (const double*)c->lam.p + lam_off[j] + (long long)side * n,
+                      (const int*)c->rank.p + rank_off[j], n, nn, 1e-12, (double*)c->eZ2t.p, s);
+        launch_gemm_nn_f64((const double*)c->eZ2t.p, n, Vs, n, G, n, nn, n, n, 1, 0, 0, 0, s);   // d2U^T
+        launch_transpose(G, nn, n, (double*)c->d2U64.p + u_off[j], s);
+      }
     }
     if (!fp64) {
       CHECK_ALLOC(dev_alloc(c, c->dU32, sizeof(float) * u_total));
@@ -1356,6 +1428,17 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     CHECK_ALLOC(dev_alloc(c, c->dTb, sizeof(double) * Rn * Rn));
     dTn = (double*)c->dT2.p;
     dTn2 = (double*)c->dTb.p;
+  }
+  // second order: the three terms of the last non-prime stage land in d2Tn, d2Tn2 (the
+  // cross term, doubled at the end) and d2Tn3
+  double *d2Tn = nullptr, *d2Tn2 = nullptr, *d2Tn3 = nullptr;
+  if (tan2) {
+    CHECK_ALLOC(dev_alloc(c, c->d2T2, sizeof(double) * Rn * Rn));
+    CHECK_ALLOC(dev_alloc(c, c->d2Tb, sizeof(double) * Rn * Rn));
+    CHECK_ALLOC(dev_alloc(c, c->d2Tc, sizeof(double) * Rn * Rn));
+    d2Tn = (double*)c->d2T2.p;
+    d2Tn2 = (double*)c->d2Tb.p;
+    d2Tn3 = (double*)c->d2Tc.p;
   }
   // the c'-slices this call contracts (all of them but in PH_CONTRACT)
   const int sl_lo = phase == PH_CONTRACT ? sh.c_lo : 0;
@@ -1400,9 +1483,9 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     // adds two more of B and C (and FP64 staging of dB in the split form) and three
     // more chain buffers
     const double per_unit =
-        (z2 ? 1.6 : 1.0) * (tangent ? (fp64 ? 3.0 : 4.0) : 1.0) * (double)(Ns / nnew1) *
+        (z2 ? 1.6 : 1.0) * (tangent ? (fp64 ? (tan2 ? 4.0 : 3.0) : 4.0) : 1.0) * (double)(Ns / nnew1) *
             ((fp64 ? 8.0 * R : (double)pbytes * npieces * Kpad) + (fp64 ? 8.0 : 4.0) * R) +
-        (tangent ? 5.0 : 2.0) * (double)elt * (double)chain_max / nnew1;
+        (tan2 ? 7.0 : (tangent ? 5.0 : 2.0)) * (double)elt * (double)chain_max / nnew1;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     double budget = std::min(0.6 * (double)free_b + (double)(c->Bp.bytes + c->Cb.bytes + c->chA.bytes +
@@ -1418,6 +1501,10 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     CHECK_ALLOC(dev_alloc(c, c->dchA, elt * chain_sub));
     CHECK_ALLOC(dev_alloc(c, c->dchB, elt * chain_sub));
     CHECK_ALLOC(dev_alloc(c, c->dchT, elt * chain_sub));
+  }
+  if (tan2) {
+    CHECK_ALLOC(dev_alloc(c, c->d2chA, elt * chain_sub));
+    CHECK_ALLOC(dev_alloc(c, c->d2chB, elt * chain_sub));
   }
   // Z2 index maps.  Rows of T and the contracted index (rho, n^') run over the same
   // slots with the same parities, so one list per parity b serves as the row map
@@ -1533,6 +1620,10 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
       CHECK_ALLOC(dev_alloc(c, c->dCb, sizeof(double) * R * Nsub));
       CHECK_ALLOC(dev_alloc(c, c->tCb, sizeof(double) * R * Nsub));
     }
+    if (tan2) {
+      CHECK_ALLOC(dev_alloc(c, c->d2Bp, sizeof(double) * Nsub * R));
+      CHECK_ALLOC(dev_alloc(c, c->d2Cb, sizeof(double) * R * Nsub));
+    }
     if (z2) {
       CHECK_ALLOC(dev_alloc(c, c->Za, sizeof(double) * (Rb[0] * Kpb[0] + Rb[1] * Kpb[1])));
       CHECK_ALLOC(dev_alloc(c, c->Zb, sizeof(double) * maxL * (Kpb[0] + Kpb[1])));
@@ -1606,6 +1697,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     for (int k = 1; k < d; ++k) in.push_back({I_NCP + k, chij[k], cs[k]});
     const void* src = Tc + (long long)sl * cs[0];
     const void* dsrc = tangent ? (const double*)c->dT.p + (long long)sl * cs[0] : nullptr;
+    const void* d2src = tan2 ? (const double*)c->d2T.p + (long long)sl * cs[0] : nullptr;
     int src_f64 = 1;
     for (int j = 1; j < d; ++j) {
       Phase ph(c, 5);
@@ -1643,6 +1735,15 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
           launch_chain_f64(cd, (const double*)dsrc, (const double*)c->U64.p + u_off[j] + ucol, ddst, s);
           launch_chain_f64(cd, (const double*)src, (const double*)c->dU64.p + u_off[j] + ucol, tdst, s);
           launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
+          if (tan2) {   // d2X_j = stage(d2X_{j-1}, U) + 2 stage(dX_{j-1}, dU) + stage(X_{j-1}, d2U)
+            double* d2dst = last ? (double*)c->d2Bp.p : (double*)((j & 1) ? c->d2chA.p : c->d2chB.p);
+            launch_chain_f64(cd, (const double*)d2src, (const double*)c->U64.p + u_off[j] + ucol, d2dst, s);
+            launch_chain_f64(cd, (const double*)dsrc, (const double*)c->dU64.p + u_off[j] + ucol, tdst, s);
+            launch_axpby(2.0, tdst, 1.0, d2dst, view_elems(out), s);
+            launch_chain_f64(cd, (const double*)src, (const double*)c->d2U64.p + u_off[j] + ucol, tdst, s);
+            launch_axpby(1.0, tdst, 1.0, d2dst, view_elems(out), s);
+            d2src = d2dst;
+          }
           dsrc = ddst;
         }
       } else if (c->f64_chains && !tangent) {
@@ -1802,6 +1903,16 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
                            (int)R, (int)Nc, R, 1, 0, s);
         launch_axpby(1.0, (const double*)c->tCb.p, 1.0, (double*)c->dCb.p, R * Nc, s);
       }
+      if (tan2) {      // d2C = T^ . d2B^T + 2 dT^ . dB^T + d2T^ . B^T
+        launch_gemm_nt_f64(Tc, R, (const double*)c->d2Bp.p, R, (double*)c->d2Cb.p, Nc, 0, (int)R, (int)Nc, R, 1,
+                           0, s);
+        launch_gemm_nt_f64((const double*)c->dT.p, R, (const double*)c->dBp.p, R, (double*)c->tCb.p, Nc, 0,
+                           (int)R, (int)Nc, R, 1, 0, s);
+        launch_axpby(2.0, (const double*)c->tCb.p, 1.0, (double*)c->d2Cb.p, R * Nc, s);
+        launch_gemm_nt_f64((const double*)c->d2T.p, R, (const double*)c->Bp.p, R, (double*)c->tCb.p, Nc, 0,
+                           (int)R, (int)Nc, R, 1, 0, s);
+        launch_axpby(1.0, (const double*)c->tCb.p, 1.0, (double*)c->d2Cb.p, R * Nc, s);
+      }
     } else {
       if (launch_tc_gemm(c->Ap.p, (int)R, c->Bp.p, (int)Nc, (int)Kpad, npieces, nterms, terms_a, terms_b,
                          (float*)c->Cb.p, Nc, &((DevState*)c->state.p)->status, s, nullptr, pfmt) != 0)
@@ -1827,6 +1938,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     for (int k = 1; k < d; ++k) cin.push_back({I_NC + k, chij[k], prod_after(chij, k)});
     const void* csrc = c->Cb.p;
     const void* dcsrc = tangent ? c->dCb.p : nullptr;
+    const void* d2csrc = tan2 ? c->d2Cb.p : nullptr;
     for (int j = d - 1; j >= 1; --j) {
       Phase ph(c, 7);
       View out;
@@ -1860,6 +1972,20 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
           launch_chain_f64(cd, (const double*)dcsrc, (const double*)c->U64.p + u_off[j], ddst, s);
           launch_chain_f64(cd, (const double*)csrc, (const double*)c->dU64.p + u_off[j], tdst, s);
           if (!last) launch_axpby(1.0, tdst, 1.0, ddst, view_elems(out), s);
+          if (tan2) {   // d2Y_j = stage(d2Y_{j+1}, U) + 2 stage(dY_{j+1}, dU) + stage(Y_{j+1}, d2U)
+            double* d2dst = last ? d2Tn + slab : (double*)((j & 1) ? c->d2chA.p : c->d2chB.p);
+            launch_chain_f64(cd, (const double*)d2csrc, (const double*)c->U64.p + u_off[j], d2dst, s);
+            if (last) {   // the other two terms in their own tensors, added at the end
+              launch_chain_f64(cd, (const double*)dcsrc, (const double*)c->dU64.p + u_off[j], d2Tn2 + slab, s);
+              launch_chain_f64(cd, (const double*)csrc, (const double*)c->d2U64.p + u_off[j], d2Tn3 + slab, s);
+            } else {
+              launch_chain_f64(cd, (const double*)dcsrc, (const double*)c->dU64.p + u_off[j], tdst, s);
+              launch_axpby(2.0, tdst, 1.0, d2dst, view_elems(out), s);
+              launch_chain_f64(cd, (const double*)csrc, (const double*)c->d2U64.p + u_off[j], tdst, s);
+              launch_axpby(1.0, tdst, 1.0, d2dst, view_elems(out), s);
+            }
+            d2csrc = d2dst;
+          }
           dcsrc = ddst;
         }
       } else if (c->f64_chains && !tangent) {
@@ -1919,6 +2045,10 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
 
   if (pending_error(c, "the non-prime chain") != HOTRG_OK) return HOTRG_ECUDA;
   if (tangent) launch_axpby(1.0, dTn2, 1.0, dTn, Rn * Rn, s);
+  if (tan2) {
+    launch_axpby(2.0, d2Tn2, 1.0, d2Tn, Rn * Rn, s);
+    launch_axpby(1.0, d2Tn3, 1.0, d2Tn, Rn * Rn, s);
+  }
   // ---- bond dims of the new tensor (Sec. 4.2.15 with the axes kept physical)
   for (int j = 1; j < d; ++j) c->chis[to[j]] = nnew[j];
   if (track)
@@ -1935,6 +2065,10 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
     if (tangent) {
       CHECK_ALLOC(dev_alloc(c, c->dT, sizeof(double) * Rn * Rn));
       tangent_trace_and_normalise(c, dTn, 0);
+    }
+    if (tan2) {
+      CHECK_ALLOC(dev_alloc(c, c->d2T, sizeof(double) * Rn * Rn));
+      tangent2_trace_and_normalise(c, d2Tn, dTn, 0);
     }
   }
 
@@ -2442,14 +2576,15 @@ int hotrg_bottleneck_flops(hotrg_ctx* c, double* dense, double* performed, int* 
 }
 
 int hotrg_set_tangent(hotrg_ctx* c, int enable) {
-  if (!c || enable < 0 || enable > 1) return HOTRG_EINVAL;
+  if (!c || enable < 0 || enable > 2) return HOTRG_EINVAL;
   if (!enable) {
     c->tangent = 0;
     return HOTRG_OK;
   }
   if (c->poisoned) return HOTRG_ESTATE;
-  if (c->tangent) return HOTRG_OK;
+  if (c->tangent == enable) return HOTRG_OK;
   if (!c->is_ising || c->p != 0 || !(c->beta > 0.0)) return HOTRG_EINVAL;
+  if (enable == 2 && c->precision != HOTRG_PREC_FP64) return HOTRG_EINVAL;   // second order: FP64 form
   const long long n = tensor_elems(c);
   CHECK_ALLOC(dev_alloc(c, c->tstate, sizeof(TanState)));
   CHECK_ALLOC(dev_alloc(c, c->Yd, sizeof(double) * kMaxBond * kMaxBond));
@@ -2458,8 +2593,27 @@ int hotrg_set_tangent(hotrg_ctx* c, int enable) {
   cudaMemsetAsync(c->tstate.p, 0, sizeof(TanState), c->stream);
   launch_init_ising_dbeta((double*)c->dT2.p, c->d, c->beta, c->h, c->stream);
   tangent_trace_and_normalise(c, (const double*)c->dT2.p, 1);
-  c->tangent = 1;
+  if (enable == 2) {
+    CHECK_ALLOC(dev_alloc(c, c->Yd2, sizeof(double) * kMaxBond * kMaxBond));
+    CHECK_ALLOC(dev_alloc(c, c->d2T2, sizeof(double) * n));
+    CHECK_ALLOC(dev_alloc(c, c->d2T, sizeof(double) * n));
+    launch_init_ising_d2beta((double*)c->d2T2.p, c->d, c->beta, c->h, c->stream);
+    tangent2_trace_and_normalise(c, (const double*)c->d2T2.p, (const double*)c->dT2.p, 1);
+  }
+  c->tangent = enable;
   return cuda_status(c);
+}
+
+int hotrg_specific_heat(hotrg_ctx* c, double* d2lnz_dbeta2, double* specific_heat) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->tangent != 2) return HOTRG_ESTATE;
+  int r = sync_and_status(c, nullptr);
+  if (r != HOTRG_OK) return r;
+  TanState t;
+  if (cudaMemcpy(&t, c->tstate.p, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_status(c);
+  if (d2lnz_dbeta2) *d2lnz_dbeta2 = t.d2ln_z_site;
+  if (specific_heat) *specific_heat = c->beta * c->beta * t.d2ln_z_site;
+  return HOTRG_OK;
 }
 
 int hotrg_energy(hotrg_ctx* c, double* dlnz_dbeta, double* energy, int* degenerate_pairs) {
@@ -2577,7 +2731,9 @@ void hotrg_free(hotrg_ctx* c) {
               &c->J32,  &c->Gns, &c->Vtmp, &c->Za, &c->Zb, &c->Zc, &c->Zmap, &c->Zg, &c->Eb,
               &c->dT, &c->dT2, &c->dTb, &c->dXp, &c->dS, &c->dA, &c->dU64, &c->eG, &c->eZ, &c->eZt,
               &c->rank, &c->Yd, &c->tstate, &c->dchA, &c->dchB, &c->dchT, &c->dBp, &c->tBp, &c->dCb,
-              &c->tCb, &c->dAp, &c->dB64, &c->dU32};
+              &c->tCb, &c->dAp, &c->dB64, &c->dU32, &c->d2T, &c->d2T2, &c->d2Tb, &c->d2Tc, &c->d2Xp,
+              &c->d2S, &c->d2A, &c->d2U64, &c->eG1, &c->eW, &c->eZ2, &c->eZ2t, &c->d2chA, &c->d2chB,
+              &c->d2Bp, &c->d2Cb, &c->Yd2, &c->parts2};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);

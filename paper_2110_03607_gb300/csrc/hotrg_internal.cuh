@@ -34,6 +34,9 @@ struct TanState {
   double dtrace;       // Tr dT^(p)
   int degenerate;      // eigen pairs across the cut with no derivative (left out)
   int pad;
+  double d2kappa;      // d^2 kappa_p / d beta^2 (second order carried)
+  double d2ln_tr;      // d^2 ln Tr T^(p) / d beta^2
+  double d2ln_z_site;  // d^2 (ln Z^(p) / 2^p) / d beta^2
 };
 
 // Per-leg results of the isometry selection.
@@ -298,5 +301,15 @@ void launch_finish_tangent(const double* Yd, int chi_c, const DevState* st, TanS
                            cudaStream_t s);
 void launch_tangent_scale(const double* dT, const double* That, double* out, long long n, const DevState* st,
                           const TanState* tst, cudaStream_t s);
+// second order (d^2 / d beta^2)
+void launch_init_ising_d2beta(double* d2T, int d, double beta, double h, cudaStream_t s);
+void launch_assemble_ddot(const double* sh, const double* dsh, const double* d2sh, const double* sc,
+                          const double* dsc, const double* d2sc, int chi_j, int chi_c, double* d2A, cudaStream_t s);
+void launch_eig_d2(const double* G1, const double* Gs, const double* G2s, const double* lam_sorted, const int* rank,
+                   int n, int nnew, double rel_tol, double* Z2t, cudaStream_t s);
+void launch_finish_tangent2(const double* Yd2, int chi_c, const DevState* st, TanState* tst, int p, int first,
+                            cudaStream_t s);
+void launch_tangent2_scale(const double* d2T, const double* dT, const double* dThat, const double* That, double* out,
+                           long long n, const DevState* st, const TanState* tst, cudaStream_t s);
 
 }  // namespace hotrg

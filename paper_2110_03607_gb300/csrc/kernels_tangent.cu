@@ -222,4 +222,172 @@ void launch_tangent_scale(const double* dT, const double* That, double* out, lon
   ++g_launches;
 }
 
+// ---------------------------------------------------------------------------
+// Second derivative d^2 / d beta^2 (specific heat), carried beside T and dT
+// ---------------------------------------------------------------------------
+
+// d^2 T0 / d beta^2 of Eq. (2.4): per sigma the product over the field factor
+// V = exp(beta h sigma) and the 2d legs, differentiated twice by the product rule
+// (P'' <- P'' g + 2 P' g' + P g'' for each factor g); x_0 = sqrt(cosh), x_1 = sigma
+// sqrt(sinh), x_0'' = sqrt(cosh) / 2 - sinh^2 / (4 cosh^{3/2}), x_1'' = sigma (sqrt(sinh) / 2 -
+// cosh^2 / (4 sinh^{3/2})), V'' = h^2 V.
+__global__ void init_ising_d2beta_kernel(double* d2T, int d, double beta, double h) {
+  const int n = 1 << (2 * d);
+  const double c = cosh(beta), sh = sinh(beta);
+  const double x0 = sqrt(c), x1 = sqrt(sh);
+  const double dx0 = sh / (2.0 * x0), dx1 = c / (2.0 * x1);
+  const double ddx0 = 0.5 * x0 - sh * sh / (4.0 * c * x0), ddx1 = 0.5 * x1 - c * c / (4.0 * sh * x1);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < 2; ++s) {
+      const double sigma = s == 0 ? 1.0 : -1.0;
+      const double bw = exp(beta * h * sigma);
+      double p0 = bw, p1 = h * sigma * bw, p2 = h * h * bw;
+      for (int leg = 0; leg < 2 * d; ++leg) {
+        const int bit = (e >> leg) & 1;
+        const double g0 = bit ? sigma * x1 : x0, g1 = bit ? sigma * dx1 : dx0, g2 = bit ? sigma * ddx1 : ddx0;
+        p2 = p2 * g0 + 2.0 * p1 * g1 + p0 * g2;
+        p1 = p1 * g0 + p0 * g1;
+        p0 *= g0;
+      }
+      acc += p2;
+    }
+    d2T[e] = acc;
+  }
+}
+
+void launch_init_ising_d2beta(double* d2T, int d, double beta, double h, cudaStream_t s) {
+  init_ising_d2beta_kernel<<<1, 256, 0, s>>>(d2T, d, beta, h);
+  ++g_launches;
+}
+
+// d^2 A = sum_{rho eta} (d2S^ S~ + 2 dS^ dS~ + S^ d2S~) (Sec. 3.2 assembly, index conventions of
+// assemble_dot_kernel)
+__global__ void assemble_ddot_kernel(const double* __restrict__ sh, const double* __restrict__ dsh,
+                                     const double* __restrict__ d2sh, const double* __restrict__ sc,
+                                     const double* __restrict__ dsc, const double* __restrict__ d2sc, int chi,
+                                     int chc, double* __restrict__ d2A) {
+  const int n = chi * chi, m = chi * chc;
+  const long long total = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i > j) continue;
+    const int fh = i % chi, fc = i / chi, gh = j % chi, gc = j / chi;
+    const long long oh = (long long)(fh * chc) * m + gh * chc, oc = (long long)(fc * chc) * m + gc * chc;
+    double acc = 0.0;
+    for (int rho = 0; rho < chc; ++rho)
+      for (int eta = 0; eta < chc; ++eta) {
+        const long long k = (long long)rho * m + eta;
+        acc = fma(d2sh[oh + k], sc[oc + k], acc);
+        acc = fma(2.0 * dsh[oh + k], dsc[oc + k], acc);
+        acc = fma(sh[oh + k], d2sc[oc + k], acc);
+      }
+    d2A[(long long)i * n + j] = acc;
+    d2A[(long long)j * n + i] = acc;
+  }
+}
+
+void launch_assemble_ddot(const double* sh, const double* dsh, const double* d2sh, const double* sc,
+                          const double* dsc, const double* d2sc, int chi_j, int chi_c, double* d2A, cudaStream_t s) {
+  assemble_ddot_kernel<<<tgrid((long long)chi_j * chi_j * chi_j * chi_j), 256, 0, s>>>(sh, dsh, d2sh, sc, dsc, d2sc,
+                                                                                      chi_j, chi_c, d2A);
+  ++g_launches;
+}
+
+// Second derivative of a kept isometry column in the parallel-transport gauge (U' = P' U,
+// U'' = P'' U + P' P' U, P the projector on the kept eigenvectors of A), in the eigenbasis:
+//   Z2t[k][a] = sum_b w(a, b) G1[a][b] Gs[b][k] + [a discarded] G2s[a][k] / (lam_c - lam_a)
+// with c the eigenvector kept at position k, G1[a][b] = v_a . dA v_b, Gs[b][k] = v_b . dA u_k,
+// G2s[a][k] = v_a . d2A u_k, and w the divided differences of the kept-set indicator
+// (2 chi[a, b, c] + chi[a, b] chi[b, c]):
+//   a, b kept: 0;  a kept, b not: -1 / ((lam_a - lam_b)(lam_c - lam_b));
+//   a not, b kept: -2 / ((lam_b - lam_a)(lam_c - lam_a));  a, b not: 2 / ((lam_c - lam_a)(lam_c - lam_b)).
+// A term whose kept-discarded gap is within rel_tol lam_1 is left out (no derivative there).
+__global__ void eig_d2_kernel(const double* __restrict__ G1, const double* __restrict__ Gs,
+                              const double* __restrict__ G2s, const double* __restrict__ lam_sorted,
+                              const int* __restrict__ rank, int n, int nnew, double rel_tol, double* __restrict__ Z2t) {
+  const double tol = rel_tol * lam_sorted[0];
+  const int total = n * nnew;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int k = e / n, a = e % n;
+    const double lc = lam_sorted[k];
+    const int ra = rank[a];
+    const bool ka = ra < nnew;
+    const double la = lam_sorted[ra];
+    double acc = 0.0;
+    if (!ka && fabs(lc - la) > tol) acc = G2s[(long long)a * nnew + k] / (lc - la);
+    for (int b = 0; b < n; ++b) {
+      const int rb = rank[b];
+      const bool kb = rb < nnew;
+      if (ka && kb) continue;
+      const double lb = lam_sorted[rb];
+      double w;
+      if (ka) {   // a kept, b discarded
+        const double g1 = la - lb, g2 = lc - lb;
+        if (fabs(g1) <= tol || fabs(g2) <= tol) continue;
+        w = -1.0 / (g1 * g2);
+      } else if (kb) {   // a discarded, b kept
+        const double g1 = lb - la, g2 = lc - la;
+        if (fabs(g1) <= tol || fabs(g2) <= tol) continue;
+        w = -2.0 / (g1 * g2);
+      } else {
+        const double g1 = lc - la, g2 = lc - lb;
+        if (fabs(g1) <= tol || fabs(g2) <= tol) continue;
+        w = 2.0 / (g1 * g2);
+      }
+      acc = fma(w * G1[(long long)a * n + b], Gs[(long long)b * nnew + k], acc);
+    }
+    Z2t[(long long)k * n + a] = acc;
+  }
+}
+
+void launch_eig_d2(const double* G1, const double* Gs, const double* G2s, const double* lam_sorted, const int* rank,
+                   int n, int nnew, double rel_tol, double* Z2t, cudaStream_t s) {
+  eig_d2_kernel<<<tgrid((long long)n * nnew), 256, 0, s>>>(G1, Gs, G2s, lam_sorted, rank, n, nnew, rel_tol, Z2t);
+  ++g_launches;
+}
+
+// d^2 of the trace bookkeeping, after finish_tangent has run for the same step:
+//   d2 ln Tr_p = Tr d2T^(p) / Tr T^(p) - (d ln Tr_p)^2,
+//   d2 kappa_p = d2 kappa_{p-1} + d2 ln Tr_{p-1} / 2^(p-1),  d2(ln Z^(p)/V) = d2 kappa_p + d2 ln Tr_p / 2^p
+__global__ void finish_tangent2_kernel(const double* __restrict__ Yd2, int chi_c, const DevState* st, TanState* tst,
+                                       int p, int first) {
+  if (threadIdx.x != 0) return;
+  double d2tr = 0.0;
+  for (int c = 0; c < chi_c; ++c) d2tr += Yd2[c * chi_c + c];
+  const double l1 = tst->dln_tr;
+  const double d2ln_tr = d2tr / st->trace - l1 * l1;
+  if (first) {
+    tst->d2kappa = 0.0;
+    tst->d2ln_z_site = d2ln_tr;
+  } else {
+    tst->d2kappa = tst->d2kappa + ldexp(tst->d2ln_tr, -(p - 1));
+    tst->d2ln_z_site = tst->d2kappa + ldexp(d2ln_tr, -p);
+  }
+  tst->d2ln_tr = d2ln_tr;
+}
+
+void launch_finish_tangent2(const double* Yd2, int chi_c, const DevState* st, TanState* tst, int p, int first,
+                            cudaStream_t s) {
+  finish_tangent2_kernel<<<1, 32, 0, s>>>(Yd2, chi_c, st, tst, p, first);
+  ++g_launches;
+}
+
+// d^2 (T / Tr T) = d2T / Tr - (d ln Tr) dT / Tr - (d ln Tr) d(T / Tr) - (d2 ln Tr) (T / Tr):
+// out = d2T f - l1 dT f - l1 dThat - l2 That, f = 1 / Tr
+__global__ void tangent2_scale_kernel(const double* __restrict__ d2T, const double* __restrict__ dT,
+                                      const double* __restrict__ dThat, const double* __restrict__ That,
+                                      double* __restrict__ out, long long n, const DevState* st, const TanState* tst) {
+  const double f = st->inv_trace, l1 = tst->dln_tr, l2 = tst->d2ln_tr;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = d2T[i] * f - l1 * dT[i] * f - l1 * dThat[i] - l2 * That[i];
+}
+
+void launch_tangent2_scale(const double* d2T, const double* dT, const double* dThat, const double* That, double* out,
+                           long long n, const DevState* st, const TanState* tst, cudaStream_t s) {
+  tangent2_scale_kernel<<<tgrid(n), 256, 0, s>>>(d2T, dT, dThat, That, out, n, st, tst);
+  ++g_launches;
+}
+
 }  // namespace hotrg
