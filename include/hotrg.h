@@ -291,8 +291,8 @@ int hotrg_shard_finish(hotrg_ctx* ctx, int axis, int chi, const double* slices, 
  * projector on the kept eigenvectors (in the eigenbasis: divided differences
  * of the kept-set indicator times V^T dA V and V^T d2A V; terms across a
  * degenerate cut left out as in the first order).  hotrg_specific_heat then
- * returns d^2(ln Z/V)/d beta^2.  A step costs about ten dense FP64 forward
- * steps.  Errors: EINVAL (not an Ising context, beta = 0, steps already
+ * returns d^2(ln Z/V)/d beta^2.  A step costs about twice a step carrying
+ * the first derivative only (3D chi = 12: 7.4 s against 3.7 s).  Errors: EINVAL (not an Ising context, beta = 0, steps already
  * taken, enable = 2 with a split precision), ENOMEM, ECUDA, ESTATE. */
 int hotrg_set_tangent(hotrg_ctx* ctx, int enable);
 
