@@ -32,8 +32,12 @@ namespace cg = cooperative_groups;
 namespace hotrg {
 
 __device__ __forceinline__ int rr_slot(int i, int r, int mp) {
-  // circle method: player 0 fixed, the others rotate by r
-  return i == 0 ? 0 : 1 + (i - 1 + r) % (mp - 1);
+  // circle method: player 0 fixed, the others rotate by r (0 <= i - 1 + r < 2 (mp - 1), so
+  // one conditional subtraction replaces the modulo)
+  if (i == 0) return 0;
+  int x = i - 1 + r;
+  if (x >= mp - 1) x -= mp - 1;
+  return 1 + x;
 }
 
 // NPL = ceil(n / 32): column entries held per lane
@@ -523,6 +527,7 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (m) first = k0 + __ffs(m) - 1;
       }
+      if (first >= n) first = 0;   // no entry found (a NaN column): stay in range; the trace reports it
       if (lane == 0) {
         lam[side * n + i] = sqrt(s2);
         piv[side * n + i] = first;
@@ -534,9 +539,13 @@ __global__ void __launch_bounds__(512) select_kernel(const double* __restrict__ 
   for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
     int side = e / n, i = e % n;
     const double* l = lam + side * n;
-    double li = l[i];
+    // a NaN ranks below every number, so that the ranks stay a permutation
+    const double li = isnan(l[i]) ? -1.0 : l[i];
     int rank = 0;
-    for (int k = 0; k < n; ++k) rank += (l[k] > li) || (l[k] == li && k < i);
+    for (int k = 0; k < n; ++k) {
+      const double lk = isnan(l[k]) ? -1.0 : l[k];
+      rank += (lk > li) || (lk == li && k < i);
+    }
     order[side * n + rank] = i;
   }
   __syncthreads();
