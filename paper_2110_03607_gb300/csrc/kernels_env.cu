@@ -41,6 +41,9 @@ __global__ void __launch_bounds__(256, 2) gemm_nt_f64_kernel(
     bx = ti + t;
   }
   const int n0 = bx * T, m0 = by * T;
+  // a diagonal tile of a symmetric product: output (ty + 16 i, tx + 16 j) with i > j lies
+  // below the diagonal (tx - ty <= 15), which the reductions never read; skipped block-wide
+  const bool diag = upper_only && bx == by;
   const long long k_lo = (long long)blockIdx.z * kchunk;
   long long k_hi = k_lo + kchunk;
   if (k_hi > K) k_hi = K;
@@ -82,7 +85,8 @@ __global__ void __launch_bounds__(256, 2) gemm_nt_f64_kernel(
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j)
+          if (!(diag && i > j)) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
