@@ -75,18 +75,34 @@ __global__ void __launch_bounds__(256, 2) gemm_nt_f64_kernel(
     }
     __syncthreads();
     if (k0 + BK < k_hi) fetch(k0 + BK);
+    // two bodies, so that the diagonal tiles' skipped products are not issued at all
+    // (a predicated-off FMA would still take its slot in the FP64 pipe)
+    if (diag) {
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double a[R], b[R];
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
+        for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-          if (!(diag && i > j)) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = i; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[R], b[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
