@@ -1793,6 +1793,13 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
             c->poisoned = HOTRG_EINVAL;
             return HOTRG_EINVAL;
           }
+          // the output row of a thread: sum of its row-dim indices times their strides / Kpad
+          for (int q1 = 0; q1 < kMaxDims; ++q1) zo.rstride[q1] = q1 >= q0 && q1 < cd.ndim ? cd.out_stride[q1] / Kpad : 0;
+          // t / R by multiply-shift, as for the dims (make_stage)
+          int l = 0;
+          while ((1ULL << l) < (unsigned long long)R) ++l;
+          zo.r_shift = l;
+          zo.r_magic = (unsigned)((((1ULL << l) - (unsigned long long)R) << 32) / (unsigned long long)R + 1);
         }
         launch_chain_f32_z2out(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, zo, s);
       } else {

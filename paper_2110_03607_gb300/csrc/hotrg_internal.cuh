@@ -214,6 +214,9 @@ struct Z2Out {
   long long pstride[2];   // piece stride of block b
   long long kpad;         // row pitch of the dense out view
   long long nrow_step;    // rows between consecutive values of the stage's new index
+  unsigned r_magic;       // t / R = (umulhi(t, r_magic) + t) >> r_shift
+  int r_shift;
+  long long rstride[kMaxDims];   // per free dim: its out stride / kpad (0 for the k dims)
 };
 
 // First non-prime stage read straight from the Z2 blocks of the bottleneck's product C.

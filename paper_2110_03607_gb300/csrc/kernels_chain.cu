@@ -71,11 +71,11 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
     unsigned kidx = 0;
     if (OUT == OUT_Z2_SPLIT || OUT == OUT_Z2_SPLIT_W) {
       // t = (row group, list position): the thread's dense k comes from the K lists
-      const unsigned grp = rem / zo.R;
+      const unsigned grp = (unsigned)(((unsigned long long)__umulhi(rem, zo.r_magic) + rem) >> zo.r_shift);
       kidx = rem - grp * zo.R;
       rem = grp * zo.R + (unsigned)zo.kcat[kidx];
     }
-    long long in_off = 0, out_off = 0;
+    long long in_off = 0, out_off = 0, orow = 0;   // orow: the output row (Z2 outputs)
     int a_val = 0;
 #pragma unroll
     for (int k = 0; k < kMaxDims; ++k) {
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
       rem = q;
       in_off += (long long)idx * d.in_stride[k];
       out_off += (long long)idx * d.out_stride[k];
+      if (OUT == OUT_Z2_SPLIT || OUT == OUT_Z2_SPLIT_W) orow += (long long)idx * zo.rstride[k];
       if (k == d.a_dim) a_val = (int)idx;
     }
     // OUT_Z2_SPLIT_W: the warp's threads share the output rows row0 + n nrow_step; lane n
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
     if (OUT == OUT_Z2_SPLIT_W) {
       const int ln = threadIdx.x & 31;
       if (ln < NN && ln < d.nn) {
-        const long long row = out_off / zo.kpad + ln * zo.nrow_step;
+        const long long row = orow + ln * zo.nrow_step;
         zlane = (unsigned)zo.cpos[row] | ((unsigned)(zo.cblk[row] ^ zo.q) << 31);
       }
     }
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(256, (chain_min_ctas<TIn, NN, OUT, ZIN>())) ch
     } else {
       // OUT_Z2_SPLIT: consecutive threads hold consecutive positions of one K list, so
       // a warp's stores to a block row are contiguous
-      const long long row0 = out_off / zo.kpad;
+      const long long row0 = orow;
       const int kb = kidx >= zo.rb0 ? 1 : 0;
       const long long kpos = (long long)(kb ? kidx - zo.rb0 : kidx);
       // selects, not an index: an indexed parameter array would be copied to local memory
