@@ -749,6 +749,8 @@ def main():
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the two timed steps of the plain FP64 form")
     ap.add_argument("--workload", default="ising3d_chi16", choices=sorted(WORKLOADS))
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the chain stages' launch shapes on their first launch (hotrg_set_autotune)")
     ap.add_argument("--graphs", action="store_true",
                     help="batching workloads: replay captured 6-step cycles (dense steps) instead of "
                          "stepping through hotrg_step_batch")
@@ -785,6 +787,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     g = pkg.Hotrg(D, BETA, H, precision=prec, z2=args.z2 == "on")
+    if args.autotune:
+        pkg.hotrg_set_autotune(g.ctx, True)
     axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
     lnz_by_step = {}
     for i, a in enumerate(axes[: GROWTH_STEPS + args.warmup]):
@@ -835,6 +839,8 @@ def main():
     replay_same = None
     if not WORKLOAD.startswith("ising4d_chi1"):
         rp = pkg.Hotrg(D, BETA, H, precision=prec, z2=args.z2 == "on")
+        if args.autotune:
+            pkg.hotrg_set_autotune(rp.ctx, True)
         phase_sum = {}
         step_no = 0
         for i, a in enumerate(axes):
@@ -953,6 +959,7 @@ def main():
                                    f"steps {GROWTH_STEPS + args.warmup + 1}-{GROWTH_STEPS + args.warmup + K} timed",
                        "precision": args.precision,
                        "z2_blocks": args.z2 == "on",
+                       "autotune": bool(args.autotune),
                        "z2_steps_timed": z2_steps,
                        "bottleneck_flops_per_step": {"dense": bn_dense / K, "performed": bn_done / K},
                        "l2": "inputs larger than L2 (T 134 MB, per-slice operands GBs)",

@@ -138,6 +138,21 @@ int hotrg_set_slice_budget(hotrg_ctx* ctx, double bytes);
  * enable = 0 everything is dense and the parities are still tracked. */
 int hotrg_set_z2(hotrg_ctx* ctx, int enable);
 
+/* Launch-shape autotuner (the paper has no counterpart): with enable = 1, the
+ * first launch of each chain-stage shape (the tensor-times-isometry stages of
+ * Sec. 4.2.9 on the default paths) runs once per candidate grid cap (4, 8,
+ * 16, 32 CTAs per SM) on the real operands, timed with CUDA events on the
+ * context's stream (the host waits for those events: that step is not
+ * asynchronous), and the fastest is kept for the shape in the context.  A
+ * stage's output does not depend on its grid, so results are the same bit for
+ * bit with or without it.  Cached choices stay in use after enable = 0 and in
+ * captured graphs; a graph capture never tunes.  Errors: EINVAL. */
+int hotrg_set_autotune(hotrg_ctx* ctx, int enable);
+
+/* *n = number of tuned chain-stage shapes; their choices (CTAs per SM) go to
+ * choices[0 .. *n) when choices is given.  Errors: EINVAL (cap < *n). */
+int hotrg_autotune_entries(hotrg_ctx* ctx, int* n, int* choices, int cap);
+
 /* Declare the parity (0 or 1) of every index of the current tensor:
  * `parity` holds chis[0] entries for axis 0, then chis[1] for axis 1, ...
  * (the two legs of an axis share them).  Checked on the device: if an

@@ -90,6 +90,8 @@ def load():
         "hotrg_shard_finish": (I, [P, I, I, P, I64]),
         "hotrg_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "hotrg_launch_count": (I, [P, ctypes.POINTER(I64)]),
+        "hotrg_set_autotune": (I, [P, I]),
+        "hotrg_autotune_entries": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), I]),
         "hotrg_graph_capture": (I, [P, I, ctypes.POINTER(I), I, ctypes.POINTER(P)]),
         "hotrg_graph_launch": (I, [P, P]),
         "hotrg_graph_free": (None, [P]),
@@ -257,6 +259,21 @@ def hotrg_set_parity(ctx, parity):
         return
     arr = (ctypes.c_int * len(parity))(*[int(x) for x in parity])
     _check(load().hotrg_set_parity(ctx, arr), "hotrg_set_parity")
+
+
+def hotrg_set_autotune(ctx, enable: bool = True):
+    """Tune the chain stages' launch shapes on their first launch (results unchanged)."""
+    _check(load().hotrg_set_autotune(ctx, 1 if enable else 0), "hotrg_set_autotune")
+
+
+def hotrg_autotune_entries(ctx):
+    """The tuned chain-stage shapes' choices (CTAs per SM)."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.hotrg_autotune_entries(ctx, ctypes.byref(n), None, 0), "hotrg_autotune_entries")
+    buf = (ctypes.c_int * max(1, n.value))()
+    _check(lib.hotrg_autotune_entries(ctx, ctypes.byref(n), buf, max(1, n.value)), "hotrg_autotune_entries")
+    return [buf[i] for i in range(n.value)]
 
 
 def hotrg_graph_capture(ctx, axes, chi: int):

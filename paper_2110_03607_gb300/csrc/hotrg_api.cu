@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <thread>
+#include <map>
 #include <vector>
 
 #include "hotrg_internal.cuh"
@@ -116,6 +117,7 @@ bool make_stage(ChainDesc& d, const View& in, const View& out, int a_name, int b
   d.ldu = nn;
   d.npieces = 1;
   d.pfmt = PIECE_BF16;
+  d.ctas_per_sm = 16;
   if (d.total >= (1LL << 32)) return false;
   for (int k = 0; k < d.ndim; ++k) {
     // Hacker's Delight unsigned division by an invariant: l = ceil(log2 s),
@@ -202,6 +204,10 @@ struct hotrg_ctx {
   // set while hotrg_graph_capture records steps: no buffer may be (re)allocated and the
   // normalisation takes the step count from the device
   int capturing = 0;
+  // launch-shape autotuner of the chain stages (hotrg_set_autotune): stage shape -> CTAs per SM
+  int autotune = 0;
+  std::map<std::vector<long long>, int> tune_cache;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -254,6 +260,42 @@ cudaEvent_t next_event(hotrg_ctx* c) {
 // RAII phase mark: records a start/stop event pair on the stream when profiling
 // Events around one part of a step: every part (profile 1), or the bottleneck GEMM
 // launches only (profile 2, phase 6), kept across steps until hotrg_step_times reads them
+// A chain stage launched with the grid cap (CTAs per SM) the autotuner chose for its shape:
+// on the first launch of a shape with autotuning on, each candidate runs once on the real
+// operands (a stage writes its output from its inputs, so the runs are idempotent and give
+// the same bits), timed with CUDA events; the fastest is kept for the context.  Without
+// autotuning, or while a graph is captured, a cached choice is used if there is one, else 16.
+template <typename F>
+void tuned_chain(hotrg_ctx* c, ChainDesc& cd, int kind, F&& launch) {
+  std::vector<long long> key = {kind, cd.total, cd.nn, cd.chi, cd.ndim, cd.a_dim};
+  for (int k = 0; k < cd.ndim; ++k) key.push_back(cd.size[k]);
+  auto it = c->tune_cache.find(key);
+  cd.ctas_per_sm = it != c->tune_cache.end() ? it->second : 16;
+  if (!c->autotune || c->capturing || it != c->tune_cache.end()) {
+    launch();
+    return;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!c->tune_ev[i]) cudaEventCreate(&c->tune_ev[i]);
+  static const int cand[4] = {4, 8, 16, 32};
+  float best = 1e30f;
+  int choice = 16;
+  for (int i = 0; i < 4; ++i) {
+    cd.ctas_per_sm = cand[i];
+    cudaEventRecord(c->tune_ev[0], c->stream);
+    launch();
+    cudaEventRecord(c->tune_ev[1], c->stream);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(c->tune_ev[1]) == cudaSuccess) cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]);
+    if (ms < best) {
+      best = ms;
+      choice = cand[i];
+    }
+  }
+  c->tune_cache[key] = choice;
+  cd.ctas_per_sm = choice;
+}
+
 struct Phase {
   hotrg_ctx* c;
   int id;
@@ -653,6 +695,22 @@ int hotrg_set_allocator(hotrg_ctx* c, hotrg_alloc_fn alloc, hotrg_free_fn free_f
   CHECK_ALLOC(dev_alloc(c, c->Y, sizeof(double) * kMaxBond * kMaxBond));
   if (c->tangent) CHECK_ALLOC(dev_alloc(c, c->Yd, sizeof(double) * kMaxBond * kMaxBond));
   if (c->tangent == 2) CHECK_ALLOC(dev_alloc(c, c->Yd2, sizeof(double) * kMaxBond * kMaxBond));
+  return HOTRG_OK;
+}
+
+int hotrg_set_autotune(hotrg_ctx* c, int enable) {
+  if (!c || enable < 0 || enable > 1) return HOTRG_EINVAL;
+  c->autotune = enable;
+  return HOTRG_OK;
+}
+
+int hotrg_autotune_entries(hotrg_ctx* c, int* n, int* choices, int cap) {
+  if (!c || !n) return HOTRG_EINVAL;
+  *n = (int)c->tune_cache.size();
+  if (!choices) return HOTRG_OK;
+  if (cap < *n) return HOTRG_EINVAL;
+  int i = 0;
+  for (const auto& kv : c->tune_cache) choices[i++] = kv.second;
   return HOTRG_OK;
 }
 
@@ -1801,13 +1859,15 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
           zo.r_shift = l;
           zo.r_magic = (unsigned)((((1ULL << l) - (unsigned long long)R) << 32) / (unsigned long long)R + 1);
         }
-        launch_chain_f32_z2out(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, zo, s);
+        tuned_chain(c, cd, 1, [&] { launch_chain_f32_z2out(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, zo, s); });
       } else {
         cd.npieces = npieces;
         cd.pfmt = pfmt;
         cd.piece_stride = Nc * Kpad;
-        launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, dst,
-                         last ? OUT_BF16_SPLIT : OUT_F32, s);
+        tuned_chain(c, cd, last ? 3 : 4, [&] {
+          launch_chain_f32(cd, src, src_f64, (const float*)c->U32.p + u_off[j] + ucol, dst,
+                           last ? OUT_BF16_SPLIT : OUT_F32, s);
+        });
         if (tangent) {   // the same in FP32; the last stage sums in FP64 (row pitch R), then splits
           ChainDesc cdt = cd;
           if (last) {
@@ -2008,7 +2068,7 @@ int step_impl(hotrg_ctx* c, int axis, int chi, const Shard& sh) {
         zi.c[0] = (const float*)cblk_cur[0];
         zi.c[1] = (const float*)cblk_cur[1];
         zi.ld = ldz;
-        launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
+        tuned_chain(c, cd, 2, [&] { launch_chain_f32_z2in(cd, zi, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s); });
       } else {
         launch_chain_f32(cd, csrc, 0, (const float*)c->U32.p + u_off[j], dst, last ? OUT_F64 : OUT_F32, s);
         if (tangent) {   // the same in FP32 (FP64 output of the last stage)
@@ -2743,6 +2803,8 @@ void hotrg_free(hotrg_ctx* c) {
               &c->d2Bp, &c->d2Cb, &c->Yd2, &c->parts2};
   for (auto* x : b) dev_release(c, *x);
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  for (auto e : c->tune_ev)
+    if (e) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);
   if (c->hpin_ev) cudaEventDestroy(c->hpin_ev);
   delete c;

@@ -70,6 +70,7 @@ struct ChainDesc {
   long long piece_stride;  // split outputs: distance between pieces (elements)
   int npieces;
   int pfmt;                // split outputs: PIECE_BF16 or PIECE_TF32
+  int ctas_per_sm;         // grid cap of the launch: this many CTAs per SM (results do not depend on it)
 };
 
 // ---- operand pieces of the split forms: x = x_0 + x_1 + ..., x_0 = x rounded to the

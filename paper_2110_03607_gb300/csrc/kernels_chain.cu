@@ -276,7 +276,7 @@ static void launch_one(const ChainDesc& d, const TIn* in, const TAcc* U, void* o
     cudaFuncSetAttribute(chain_kernel<TIn, TAcc, NN, OUT, ZIN, ZW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   long long blocks = (d.total + 255) / 256;
-  const long long cap = 16LL * sm_count();
+  const long long cap = (long long)(d.ctas_per_sm > 0 ? d.ctas_per_sm : 16) * sm_count();
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   chain_kernel<TIn, TAcc, NN, OUT, ZIN, ZW><<<(unsigned)blocks, 256, smem, s>>>(d, in, U, out, zi, zo);
