@@ -3,7 +3,7 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|bf16x3|tf32x3|tf32|fp64]
                     [--workload ising3d_chi16|ising3d_chi20|ising4d_chi6|ising4d_chi13|ising4d_chi14|
                                 batch3d_mixed|energy3d_chi12|energy3d_chi12_scan]
-                    [--z2 on|off] [--impl ours|reference]
+                    [--z2 on|off] [--shard] [--impl ours|reference]
 
 Default workload: 3D Ising, d = 3, chi = 16, beta = 0.2216544, h = 0, axes cycling
 z, x, y.  The first steps grow the bonds (2 -> 4 -> 16 for the default) and are not
@@ -21,7 +21,12 @@ differences of FP64 runs; energy3d_chi12_scan: 32 beta in [0.21, 0.23] with ener
 specific heat).
 
 Multi-GPU: independent replicas (one run per rank), weak scaling, no
-collective on the data path; rank 0 prints one JSON line.
+collective on the data path; rank 0 prints one JSON line.  With --shard every
+rank takes part in ONE run instead: each step is split by c'-slices over the
+ranks (paper_2110_03607_gb300/shard.py: this rank's part of the environment
+Grams, an NCCL all_reduce, the isometries, this rank's c'-slices of the new
+tensor, an NCCL all_gather), strong scaling; at N = 1 it runs over a
+one-rank NCCL group.
 """
 
 from __future__ import annotations
@@ -737,6 +742,119 @@ def energy_scan_arm(args):
     return 0
 
 
+def shard_arm(args):
+    """One run, its steps split by c'-slices over the ranks (NCCL collectives)."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2110_03607_gb300 as pkg
+    from paper_2110_03607_gb300 import shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world == 1 and "MASTER_PORT" not in os.environ:
+        so = socket.socket()
+        so.bind(("127.0.0.1", 0))
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ["MASTER_PORT"] = str(so.getsockname()[1])
+        so.close()
+        dist.init_process_group("nccl", rank=0, world_size=1)
+    else:
+        dist.init_process_group("nccl")
+    rank = dist.get_rank()
+    prec = prec_const(pkg, args.precision)
+    stream = torch.cuda.current_stream()
+
+    g = pkg.Hotrg(D, BETA, H, precision=prec, z2=args.z2 == "on")
+    axes = axes_for(GROWTH_STEPS + args.warmup + args.steps)
+    lnz_by_step = {}
+    for i, a in enumerate(axes[: GROWTH_STEPS + args.warmup]):
+        shard.step_sharded(g.ctx, a, CHI)
+        lnz_by_step[i + 1] = g.free_energy()[0]
+    timed_axes = axes[GROWTH_STEPS + args.warmup:]
+    pkg.hotrg_profile(g.ctx, 2)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    bn_done = 0.0
+    launches0 = pkg.hotrg_launch_count(g.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    lnz_timed = []
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for a in timed_axes:
+        shard.step_sharded(g.ctx, a, CHI)            # synchronous: collectives between calls
+        bn_done += pkg.hotrg_bottleneck_flops(g.ctx)[1]
+        lnz_timed.append(g.free_energy()[0])         # 16-byte read-back after the gather
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    launches = pkg.hotrg_launch_count(g.ctx) - launches0
+    sampler.stop()
+    clocks = sampler.summary()
+    gemm_ms, gemm_n, _ = pkg.hotrg_step_times(g.ctx)
+    pkg.hotrg_profile(g.ctx, 0)
+    K = len(timed_axes)
+    for i, v in enumerate(lnz_timed):
+        lnz_by_step[GROWTH_STEPS + args.warmup + i + 1] = v
+    golden = load_golden()
+    errs = {s: abs(lnz_by_step[s] - golden[s]) / abs(golden[s]) for s in lnz_by_step if s in golden}
+    g.close()
+
+    # roofline of this rank's bottleneck GEMM launches (its share of the c'-slices)
+    peaks, peak_src = load_peaks()
+    bn_launches = gemm_n.get("bottleneck", 0)
+    bn_ms = gemm_ms.get("bottleneck", 0.0) / max(1, bn_launches)
+    achieved = (bn_done / max(1, bn_launches)) / (bn_ms / 1000.0) / 1e12 if bn_ms > 0 else None
+    _, nterms, rate, _ = PRECISIONS[args.precision]
+    if args.precision == "fp64":
+        peak = pkg.hotrg_fp64_rate()
+        roof = {"bound": "alu", "peak_source": "FP64 FMA rate measured in this run (hotrg_fp64_rate)"}
+    else:
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * rate
+        roof = {"bound": "tensor", "peak_source": f"bf16_tflops_sustained of {peak_src}"
+                + ("" if rate == 1.0 else f" x {rate:.4f} (TF32 / BF16 nominal dense rate)")}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak if achieved else None, "traffic": None,
+                 "avg_launch_ms": bn_ms, "launches_per_step": bn_launches / K})
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": K / (elapsed_ms / 1000.0), "unit": "steps/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": PRECISIONS[args.precision][3],
+            "data": "synthetic (Ising initial tensor from beta, h; no dataset)",
+            "config": {"workload": W["text"] + f"; steps 1-{GROWTH_STEPS} (bond growth) untimed, "
+                                   f"{args.warmup} warm-up steps, "
+                                   f"steps {GROWTH_STEPS + args.warmup + 1}-{GROWTH_STEPS + args.warmup + K} timed",
+                       "precision": args.precision, "z2_blocks": args.z2 == "on",
+                       "l2": "inputs larger than L2 (T 134 MB, per-slice operands GBs)",
+                       "parallelism": f"c'-slice shard x{world} (NCCL all_reduce of the Grams, "
+                                      f"all_gather of the new tensor's slices)"},
+            "timing": "each timed step is the synchronous sharded step with its two collectives "
+                      "and a 16-byte ln Z read-back",
+            "rel_err_lnz_per_site_vs_oracle": max(errs.values()) if errs else None,
+            "rel_err_steps_compared": len(errs),
+            "roofline": roof,
+            "e2e": None,
+            "e2e_note": "the sharded step is host-synchronous already; the end-to-end number of the "
+                        "one-process step is the default arm's",
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -756,6 +874,9 @@ def main():
                          "stepping through hotrg_step_batch")
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host workers of the batching form (batch3d_mixed)")
+    ap.add_argument("--shard", action="store_true",
+                    help="split each step of ONE run by c'-slices over the ranks (NCCL; strong scaling) "
+                         "instead of running independent replicas")
     ap.add_argument("--z2", default="on", choices=["on", "off"],
                     help="Z2 block form of the contraction (on) or the paper's dense form (off)")
     args = ap.parse_args()
@@ -764,6 +885,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.shard:
+        if args.workload not in ("ising3d_chi16", "ising3d_chi20", "ising4d_chi6"):
+            ap.error("--shard: the ising3d_chi16, ising3d_chi20 and ising4d_chi6 workloads")
+        return shard_arm(args)
     if args.workload == "batch3d_mixed":
         return batch_arm(args)
     if args.workload == "energy3d_chi12":
