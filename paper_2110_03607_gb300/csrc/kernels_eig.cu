@@ -86,6 +86,10 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
     if (lane == 0 && a > 0.0) atomicMax(colmax + mat, (unsigned long long)__double_as_longlong(a));
   }
   grid.sync();
+  // fixed for the whole solve: read once into shared memory (nmat <= 16)
+  __shared__ double s_amax[16];
+  if ((int)threadIdx.x < nmat) s_amax[threadIdx.x] = __longlong_as_double((long long)__ldcg(colmax + threadIdx.x));
+  __syncthreads();
   // the computed inner product carries rounding of order n eps sqrt(a b): a
   // tolerance below that level would keep rotating rounding noise forever.  A pair
   // is rotated only if |g| > tol max(a, b), not tol sqrt(a b): the rotation it would
@@ -110,17 +114,29 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
         if (p > q) { int t = p; p = q; q = t; }
         double* wp = W + mat * nn + (long long)p * n;
         double* wq = W + mat * nn + (long long)q * n;
+        double* vp = V + mat * nn + (long long)p * n;
+        double* vq = V + mat * nn + (long long)q * n;
+        // up to 256 rows the V columns are loaded with the W columns (independent loads,
+        // one L2 round trip on the pair's path instead of two); used only if it rotates
+        constexpr bool kVreg = NPL <= 8;
+        double vxs[kVreg ? NPL : 1], vys[kVreg ? NPL : 1];
         double a = 0.0, b = 0.0, g = 0.0;
         double xs[NPL], ys[NPL];
 #pragma unroll
         for (int u = 0; u < NPL; ++u) {
           int i = lane + 32 * u;
-          double x = i < n ? __ldcg(wp + i) : 0.0, y = i < n ? __ldcg(wq + i) : 0.0;
-          xs[u] = x;
-          ys[u] = y;
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          g = fma(x, y, g);
+          xs[u] = i < n ? __ldcg(wp + i) : 0.0;
+          ys[u] = i < n ? __ldcg(wq + i) : 0.0;
+          if constexpr (kVreg) {
+            vxs[u] = i < n ? __ldcg(vp + i) : 0.0;
+            vys[u] = i < n ? __ldcg(vq + i) : 0.0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+          a = fma(xs[u], xs[u], a);
+          b = fma(ys[u], ys[u], b);
+          g = fma(xs[u], ys[u], g);
         }
         for (int o = 16; o > 0; o >>= 1) {
           a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -130,7 +146,7 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
         const double big = fmax(a, b);
         bool rot = (g != 0.0) && big > 1e-280 && (fabs(g) > tol * big);
         if (!rot) continue;
-        const bool counts = big > tol * tol * __longlong_as_double((long long)__ldcg(colmax + mat));
+        const bool counts = big > tol * tol * s_amax[mat];
         double zeta = (b - a) / (2.0 * g);
         double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t);
@@ -143,12 +159,21 @@ __global__ void __launch_bounds__(256) jacobi_onesided_kernel(double* W, double*
             __stcg(wq + i, s * xs[u] + c * ys[u]);
           }
         }
-        double* vp = V + mat * nn + (long long)p * n;
-        double* vq = V + mat * nn + (long long)q * n;
-        for (int i = lane; i < n; i += 32) {
-          double x = __ldcg(vp + i), y = __ldcg(vq + i);
-          __stcg(vp + i, c * x - s * y);
-          __stcg(vq + i, s * x + c * y);
+        if constexpr (kVreg) {
+#pragma unroll
+          for (int u = 0; u < NPL; ++u) {
+            int i = lane + 32 * u;
+            if (i < n) {
+              __stcg(vp + i, c * vxs[u] - s * vys[u]);
+              __stcg(vq + i, s * vxs[u] + c * vys[u]);
+            }
+          }
+        } else {
+          for (int i = lane; i < n; i += 32) {
+            double x = __ldcg(vp + i), y = __ldcg(vq + i);
+            __stcg(vp + i, c * x - s * y);
+            __stcg(vq + i, s * x + c * y);
+          }
         }
         if (lane == 0 && counts) atomicAdd(cur + mat, 1);
       }
