@@ -1,5 +1,6 @@
-"""The multi-GPU path of bench.py is replicas only (independent runs, no collective on
-the data path): the timing reduction and the whole-job rate, on two gloo ranks (CPU)."""
+"""The default multi-GPU path of bench.py runs replicas (independent runs, no collective on
+the data path): the timing reduction and the whole-job rate, on two gloo ranks (CPU); and
+the argument check of its sharded form (--shard, one run split over NCCL ranks)."""
 
 import os
 import socket
@@ -50,3 +51,18 @@ def test_single_process_needs_no_group():
 
     assert bench.max_over_ranks(42.0) == 42.0
     assert bench.whole_job_rate(24, 1, 2000.0) == pytest.approx(12.0)
+
+
+def test_shard_flag_refuses_workloads_it_does_not_time():
+    # bench.py --shard times the c'-slice shard of one run (NCCL); the batching and
+    # differentiation workloads have no sharded form, and the refusal comes from the
+    # argument check before any device is touched
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for wl in ("batch3d_mixed", "energy3d_chi12"):
+        r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--shard", "--workload", wl],
+                           capture_output=True, text=True, timeout=120)
+        assert r.returncode == 2, r.stderr
+        assert "--shard" in r.stderr
