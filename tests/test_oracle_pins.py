@@ -48,6 +48,7 @@ def test_initial_tensor_closed_form(d):
 
 EXACT_CASES = [
     (2, 2, 4), (2, 4, 16), (3, 3, 16),
+    (4, 2, 16),     # 4D: axes w, x -> the periodic 2 x 1 x 1 x 2 lattice, bonds (4, 16, 16, 4)
 ]
 
 
@@ -166,7 +167,7 @@ def _explicit_m(tp):
     return np.einsum(f"{sub_hat},{sub_chk}->{out}", tp, tp)
 
 
-@pytest.mark.parametrize("d,chi,axis", [(2, 3, 0), (3, 5, 0), (3, 3, 1)])
+@pytest.mark.parametrize("d,chi,axis", [(2, 3, 0), (3, 5, 0), (3, 3, 1), (4, 3, 0), (4, 5, 2)])
 def test_environment_truncation_and_new_tensor_match_definitions(d, chi, axis):
     r = o.HotrgRun(d, 0.3, 0.1)
     r.step((axis + d - 1) % d, 16)          # grow some bonds first
