@@ -3,7 +3,9 @@
 Each test checks the oracle against something other than itself: exact
 enumeration, transfer matrices, Onsager's solution, the high-temperature
 series, the paper's own definitions written out a second way (explicit M),
-a library eigen-solver, and invariants (isometry, Z2, K recurrence).
+a library eigen-solver, and invariants (isometry, Z2, K recurrence).  The last
+tests plant plausible mistakes in the oracle (a sign, an index, a transposed
+operand, the wrong end of the spectrum) and check that a pin catches each.
 """
 
 import math
@@ -171,7 +173,20 @@ def _explicit_m(tp):
 def test_environment_truncation_and_new_tensor_match_definitions(d, chi, axis):
     r = o.HotrgRun(d, 0.3, 0.1)
     r.step((axis + d - 1) % d, 16)          # grow some bonds first
-    tp = o.to_paper_order(r.t, axis)
+    _check_definitions(o.to_paper_order(r.t, axis), chi)
+
+
+@pytest.mark.parametrize("chis,chi,seed", [([3, 3], 4, 0), ([3, 2], 3, 1), ([2, 3, 2], 3, 2), ([3, 2, 2], 5, 3)])
+def test_definitions_hold_on_a_tensor_without_reflection_symmetry(chis, chi, seed):
+    # a Gaussian tensor has no lattice symmetry: S^ != S~ and A != A', so a mistake that
+    # swaps the copies (c for c', hat for check) cannot cancel out
+    import seeded_inputs as si
+    _check_definitions(o.to_paper_order(si.gaussian_tensor(chis, seed), 0), chi)
+
+
+def _check_definitions(tp, chi):
+    """A, A', the truncation identity and T_new of the oracle against explicit M (Sec. 2)."""
+    d = tp.ndim // 2
     m = _explicit_m(tp)
     legs = [o.choose_isometry(tp, j, chi, None) for j in range(1, d)]
     us = [leg.u for leg in legs]
@@ -326,3 +341,76 @@ def test_choice_rule_picks_smaller_discarded_sum():
         w, v = np.linalg.eigh(a)
         top = v[:, ::-1][:, :4]
         np.testing.assert_allclose(np.abs(np.linalg.svd(top.T @ leg.u)[1]), 1.0, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each plausible error in the oracle fails one of the pins above
+# ---------------------------------------------------------------------------
+
+def test_planted_sign_error_in_the_factor_matrix_fails_the_enumeration_pins(monkeypatch):
+    real = o.ising_factor_matrix
+
+    def planted(beta):
+        x = real(beta).copy()
+        x[1, 1] = -x[1, 1]          # sigma_1 carries +sqrt(sinh) instead of -sqrt(sinh)
+        return x
+
+    monkeypatch.setattr(o, "ising_factor_matrix", planted)
+    r = o.HotrgRun(2, 0.3, 0.1)
+    rec = r.step(1, 4)
+    exact = ex.brute_force_ln_z(ex.lattice_after(2, [1]), 0.3, 0.1)
+    assert abs(rec.ln_z - exact) > 1e-3 * abs(exact)
+
+
+def test_planted_index_mistake_in_the_environment_fails_the_definition_pin(monkeypatch):
+    # S~ summed over c' instead of c (the Gram of the hat copy taken twice)
+    import seeded_inputs as si
+    real = o._gram
+
+    def planted(tp, keep):
+        d = tp.ndim // 2
+        return real(tp, [2 * d - 1 if k == 2 * d - 2 else k for k in keep])
+
+    monkeypatch.setattr(o, "_gram", planted)
+    tp = o.to_paper_order(si.gaussian_tensor([3, 3], 0), 0)
+    with pytest.raises(AssertionError):
+        _check_definitions(tp, 4)
+
+
+def test_planted_transposed_isometry_fails_the_definition_pin(monkeypatch):
+    # the contraction reading U~ with (hat, check) swapped
+    import seeded_inputs as si
+    real = o.new_tensor
+
+    def planted(tp, us, progress=None):
+        swapped = []
+        for u in us:
+            c = int(round(math.sqrt(u.shape[0])))
+            swapped.append(u.reshape(c, c, -1).transpose(1, 0, 2).reshape(c * c, -1))
+        return real(tp, swapped, progress)
+
+    monkeypatch.setattr(o, "new_tensor", planted)
+    tp = o.to_paper_order(si.gaussian_tensor([3, 3], 0), 0)
+    with pytest.raises(AssertionError):
+        _check_definitions(tp, 4)
+
+
+def test_planted_wrong_end_of_the_spectrum_fails_onsager(monkeypatch):
+    # isometries built from the smallest eigenvalues instead of the largest
+    real = o.sorted_eigenpairs
+
+    def planted(a):
+        lam, v, sw = real(a)
+        return lam[::-1].copy(), v[:, ::-1].copy(), sw
+
+    monkeypatch.setattr(o, "sorted_eigenpairs", planted)
+    beta = 0.3
+    exact = ex.onsager_ln_z_per_site(beta)
+    try:
+        r = o.HotrgRun(2, beta, 0.0)
+        for a in o.cyclic_axes(2, 20):
+            rec = r.step(a, 8)
+        err = abs(rec.ln_z_per_site - exact) / exact
+    except FloatingPointError:      # the kept space can lose the whole trace
+        err = math.inf
+    assert err > 1e-6
