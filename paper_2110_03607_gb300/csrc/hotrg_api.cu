@@ -257,9 +257,6 @@ cudaEvent_t next_event(hotrg_ctx* c) {
   return c->event_pool[c->event_next++];
 }
 
-// RAII phase mark: records a start/stop event pair on the stream when profiling
-// Events around one part of a step: every part (profile 1), or the bottleneck GEMM
-// launches only (profile 2, phase 6), kept across steps until hotrg_step_times reads them
 // A chain stage launched with the grid cap (CTAs per SM) the autotuner chose for its shape:
 // on the first launch of a shape with autotuning on, each candidate runs once on the real
 // operands (a stage writes its output from its inputs, so the runs are idempotent and give
@@ -296,6 +293,9 @@ void tuned_chain(hotrg_ctx* c, ChainDesc& cd, int kind, F&& launch) {
   cd.ctas_per_sm = choice;
 }
 
+// RAII phase mark: records a start/stop event pair on the stream when profiling --
+// around every part of a step (profile 1), or around the bottleneck GEMM launches only
+// (profile 2, phase 6), kept across steps until hotrg_step_times reads them
 struct Phase {
   hotrg_ctx* c;
   int id;
