@@ -194,8 +194,13 @@ int hotrg_step_times(hotrg_ctx* ctx, double ms[16], int launches[16], int* n, in
  * dimension parameter chi >= 1 (Sec. 2: chi_j^new = min(chi_j^2, chi) on
  * every transverse leg j; the axis's own bond is unchanged).  Transverse
  * legs are labelled Next j = axis (axis + j) mod d (Sec. 3.1.2).  The new
- * tensor is normalised by 1/Tr (Secs. 4.2.14-4.2.16).  Asynchronous.
- * Errors: EINVAL (axis out of range, chi outside [1, 32]),
+ * tensor is normalised by 1/Tr (Secs. 4.2.14-4.2.16).  Asynchronous, with
+ * two exceptions that wait for the stream up to the choice of the isometries:
+ * a step that tracks Z2 leg parities (the block form at zero field) copies the
+ * kept isometries (a few hundred KB) to the host to derive the new legs'
+ * parities, and a step that carries a derivative reads the per-leg choices
+ * back.  hotrg_set_parity(ctx, NULL) drops the parities (dense steps from then
+ * on, no wait).  Errors: EINVAL (axis out of range, chi outside [1, 32]),
  * ENOMEM, ECUDA, ESTATE. */
 int hotrg_step(hotrg_ctx* ctx, int axis, int chi);
 

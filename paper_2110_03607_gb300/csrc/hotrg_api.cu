@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <system_error>
 #include <thread>
 #include <map>
 #include <vector>
@@ -2562,7 +2563,11 @@ int hotrg_step_batch(hotrg_ctx** ctxs, int n, const int* axes, const int* chis, 
     for (int i = next++; i < n; i = next++) st[i] = hotrg_step(ctxs[i], axes[i], chis[i]);
   };
   std::vector<std::thread> pool;
-  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  try {
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  } catch (const std::system_error&) {
+    // no more threads to be had: the ones started (and this one) take every context
+  }
   work();
   for (auto& th : pool) th.join();
   int first = HOTRG_OK;
