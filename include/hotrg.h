@@ -19,7 +19,8 @@
  *  - hotrg_step() only enqueues work on the context's stream and returns,
  *    except that while the leg parities are known (hotrg_set_z2) it waits
  *    once per step for the isometries, whose column parities give the new
- *    legs' parities and shape the Z2 block form of the contraction.
+ *    legs' parities and shape the Z2 block form of the contraction, and
+ *    that while a derivative is carried it waits for the per-leg choices.
  *    The read-back calls (hotrg_free_energy, hotrg_observables,
  *    hotrg_isometry, hotrg_spectrum, hotrg_tensor) synchronise that stream.
  *  - Device-side failures (a non-positive or non-finite trace, a Jacobi

@@ -68,6 +68,7 @@ def load():
         "hotrg_bond_dims": (I, [P, ctypes.POINTER(I)]),
         "hotrg_tensor": (I, [P, P, I64, ctypes.POINTER(I)]),
         "hotrg_gemm_nt": (I, [I, I, I, I, P, P, P]),
+        "hotrg_gemm_nt_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "hotrg_set_fp64_threshold": (I, [P, D]),
         "hotrg_set_slice_budget": (I, [P, D]),
         "hotrg_set_z2": (I, [P, I]),
@@ -226,6 +227,27 @@ def hotrg_gemm_nt(mode: int, a, b):
     c = np.empty((m, n), dtype=np.float64)
     _check(load().hotrg_gemm_nt(mode, m, n, k, _ptr(a), _ptr(b), _ptr(c)), "hotrg_gemm_nt")
     return c
+
+
+def hotrg_gemm_nt_noalloc(mode: int, a, b, c, stream=None):
+    """C = A . B^T into the caller's `c` with no device allocation.
+
+    a [M][K], b [N][K] and c [M][N] are CUDA float64 tensors, contiguous row-major,
+    owned by the caller; `stream` is a cudaStream_t handle (an int, e.g. a torch
+    stream's ``cuda_stream``; None = the legacy default stream).  The library
+    cannot tell a host pointer or a wrong shape from a good one, so both are
+    refused here before the call."""
+    for name, x in (("a", a), ("b", b), ("c", c)):
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if str(x.dtype) != "torch.float64" or x.dim() != 2 or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 2-d float64 tensor")
+    m, k = a.shape
+    n, k2 = b.shape
+    if k != k2 or tuple(c.shape) != (m, n):
+        raise ValueError("shapes must be a [M][K], b [N][K], c [M][N]")
+    _check(load().hotrg_gemm_nt_noalloc(mode, m, n, k, _ptr(a), _ptr(b), _ptr(c),
+                                        ctypes.c_void_p(stream or 0)), "hotrg_gemm_nt_noalloc")
 
 
 def hotrg_set_fp64_threshold(ctx, flops: float):
@@ -441,8 +463,33 @@ def hotrg_launch_count(ctx) -> int:
     return n.value
 
 
+# ctx address -> the ctypes callbacks given to hotrg_set_allocator, referenced until
+# hotrg_free (the library calls them until then)
+_ALLOCATORS = {}
+
+
+def hotrg_set_allocator(ctx, alloc=None, free=None):
+    """Route the context's device allocations through alloc(nbytes) -> device pointer
+    (an int; 0 or None on failure) and free(ptr); alloc = free = None returns to
+    cudaMalloc.  Buffers already held are released through the previous hooks first."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        cb = (_ALLOC_FN(), _FREE_FN())
+    else:
+        cb = (_ALLOC_FN(lambda nbytes, _user: alloc(int(nbytes)) or None),
+              _FREE_FN(lambda ptr, _user: free(ptr)))
+    _check(load().hotrg_set_allocator(ctx, cb[0], cb[1], None), "hotrg_set_allocator")
+    key = getattr(ctx, "value", ctx)
+    if alloc is None:
+        _ALLOCATORS.pop(key, None)
+    else:
+        _ALLOCATORS[key] = cb
+
+
 def hotrg_free(ctx):
     load().hotrg_free(ctx)
+    _ALLOCATORS.pop(getattr(ctx, "value", ctx), None)
 
 
 def hotrg_strerror(status: int) -> str:

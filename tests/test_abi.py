@@ -48,6 +48,34 @@ def test_library_loads_and_reports_errors_without_a_gpu(lib_path):
     assert lib.hotrg_init_ising(3, -0.1, 0.0, ctypes.byref(ctx)) == -1
     assert lib.hotrg_step(None, 0, 4) == -1
     assert lib.hotrg_gemm_nt(7, 1, 1, 1, None, None, None) == -1
+    assert lib.hotrg_gemm_nt_noalloc(7, 1, 1, 1, None, None, None, None) == -1
+    assert lib.hotrg_gemm_nt_noalloc(0, 0, 1, 1, None, None, None, None) == -1
+
+
+def test_binding_wraps_every_declared_entry_point():
+    from paper_2110_03607_gb300 import binding
+
+    names = _declared()
+    assert len(names) > 40
+    assert [n for n in names if not callable(getattr(binding, n, None))] == []
+
+
+def test_binding_refusals_before_the_library_call():
+    import torch
+
+    from paper_2110_03607_gb300 import binding
+
+    # host tensors would reach the kernels as device pointers: refused in the binding
+    a = torch.zeros((4, 8), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        binding.hotrg_gemm_nt_noalloc(binding.PREC_FP64, a, a, torch.zeros((4, 4), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        binding.hotrg_set_allocator(ctypes.c_void_p(), lambda n: 0, None)
+    # a null context is refused by the library before any CUDA call
+    with pytest.raises(binding.HotrgError) as e:
+        binding.hotrg_set_allocator(ctypes.c_void_p(), lambda n: 0, lambda p: None)
+    assert e.value.status == -1
+    assert binding._ALLOCATORS == {}
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
